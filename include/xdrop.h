@@ -1,0 +1,164 @@
+/*
+ * xdrop.h: C ABI of the GB300 X-drop seed-and-extend library (libxdrop.so).
+ *
+ * The operation.  For each read pair (A, B) that shares an exact seed of
+ * seed_len bases at A[seed_a..] and B[seed_b..], the library runs two
+ * X-drop extensions (seed-and-extend, Section "Related works", BELLA
+ * paragraph) and returns, for each, the best score and where it was
+ * reached.  The extension is the anti-diagonal X-drop dynamic program that
+ * the paper's GPU schedulers feed (Section "Related works", LOGAN
+ * paragraph: cells of one anti-diagonal are independent; Section
+ * "Comparison between small dataset and large dataset": Needleman-Wunsch /
+ * Smith-Waterman with X-drop).  The paper prints no recurrence; this
+ * library computes the following reading exactly (bit-exact, int32):
+ *
+ *   Extension over a[1..m], b[1..n] (right: the bases after the seed;
+ *   left: the bases before it, read backwards from the seed).  H(0,0) = 0;
+ *   R(i,j) = max(H(i-1,j-1) + s(a_i,b_j), H(i-1,j) + gap, H(i,j-1) + gap)
+ *   over predecessors that exist and are live, s = match or mismatch.  With
+ *   T_d the best score on anti-diagonals 0..d (T_0 = 0), a cell on diagonal
+ *   d = i+j is live iff R >= T_{d-1} - x; otherwise it is pruned.  The
+ *   extension ends when two consecutive diagonals are entirely pruned or
+ *   at d = m+n.  Its result is the final T and the first cell that reached
+ *   it (smallest d, then smallest i).
+ *
+ * Read layout (inputs).  2-bit codes A=0, C=1, G=2, T=3, 16 bases per
+ * uint32 word, base k of the buffer in bits 2(k mod 16)..2(k mod 16)+1 of
+ * word k/16.  read_off[r] is the first base of read r and must be a
+ * multiple of 16; read_len[r] its length.  Reads must lie inside the packed
+ * buffer, which holds fewer than 2^32 bases.
+ *
+ * Limits (XDROP_EINVAL otherwise): match > 0, mismatch <= 0, gap < 0,
+ * 0 <= x < 2^28; every |score| times (read_len[a] + read_len[b]) of a pair
+ * below 2^28; read_len < 2^28; seed_a + seed_len <= read_len[a] and
+ * seed_b + seed_len <= read_len[b]; read ids < n_reads.
+ *
+ * Threads.  xdrop_submit* may be called from many threads at once on one
+ * context; xdrop_sync may be called from any thread, once per ticket.
+ * Error messages are per thread (xdrop_last_error).
+ */
+#ifndef XDROP_H
+#define XDROP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define XDROP_OK 0
+#define XDROP_EINVAL (-1)    /* bad argument; nothing was launched          */
+#define XDROP_ENOMEM (-2)    /* exceeds the device memory budget even alone */
+#define XDROP_ECUDA (-3)     /* a CUDA call failed; see xdrop_last_error    */
+#define XDROP_ETIMEDOUT (-4) /* sync timed out; the ticket stays valid      */
+#define XDROP_EBUSY (-5)     /* budget taken by work in flight; retry later */
+
+/* xdrop_init flags. */
+#define XDROP_MODE_BATCHED 0u /* default: binned persistent launch in a graph */
+#define XDROP_MODE_PLAIN 1u   /* one launch per 10,000-pair sub-batch         */
+
+/* xdrop_result.status values (per pair). */
+#define XDROP_STATUS_OK 0
+#define XDROP_STATUS_INVALID 1 /* device submit only: pair failed the limits */
+
+typedef struct xdrop_ctx xdrop_ctx;   /* opaque, owned by the library */
+typedef uint64_t xdrop_ticket;
+
+typedef struct {
+    int32_t match, mismatch, gap, x;
+} xdrop_scoring;
+
+typedef struct {
+    uint32_t a, b;           /* read ids                          */
+    uint32_t seed_a, seed_b; /* 0-based seed start on each read   */
+    uint32_t seed_len;       /* seed length in bases              */
+} xdrop_pair;                /* 20 bytes, no padding              */
+
+typedef struct {
+    int32_t left_score;   /* best score of the left extension           */
+    int32_t left_begin_a; /* seed_a - i* of the left extension          */
+    int32_t left_begin_b; /* seed_b - j*                                */
+    int32_t right_score;  /* best score of the right extension          */
+    int32_t right_end_a;  /* seed_a + seed_len + i* (end, exclusive)    */
+    int32_t right_end_b;  /* seed_b + seed_len + j*                     */
+    int32_t status;       /* XDROP_STATUS_*                             */
+} xdrop_result;           /* 28 bytes                                   */
+
+typedef struct {
+    double kernel_ms;        /* device time of the last completed ticket's
+                                alignment launches (CUDA events)          */
+    uint64_t tasks;          /* extensions (2 per pair)                   */
+    uint64_t overflow_tasks; /* extensions re-run with a wider band tile  */
+    uint64_t wide_tasks;     /* extensions that needed the unbounded tier */
+    uint32_t launches;       /* kernel launches of that ticket            */
+    uint32_t graph_replays;  /* CUDA graph launches of that ticket        */
+} xdrop_stats;
+
+/* Create a context on CUDA device `device`.  device_mem_budget bounds the
+ * device memory the context holds at once (0: no bound).  flags:
+ * XDROP_MODE_*.  On success *out owns a stream, events and buffers; free
+ * it with xdrop_free.  Returns XDROP_OK, XDROP_EINVAL or XDROP_ECUDA. */
+int xdrop_init(xdrop_ctx **out, int device, size_t device_mem_budget,
+               uint32_t flags);
+
+/* Align n_pairs pairs held in HOST memory (any host memory).  The inputs
+ * are copied before the call returns; the caller may reuse them at once.
+ * `out` (n_pairs results, host memory) belongs to the caller and must stay
+ * valid until xdrop_sync(ticket) returns XDROP_OK; it is written during
+ * that sync.  All pairs are validated first: any failure returns
+ * XDROP_EINVAL and launches nothing.  n_pairs == 0 is valid (the ticket
+ * completes at once).  Returns XDROP_OK and a ticket, or an error. */
+int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
+                 const uint32_t *read_len, uint32_t n_reads,
+                 const xdrop_pair *pairs, size_t n_pairs,
+                 const xdrop_scoring *s, xdrop_result *out, xdrop_ticket *t);
+
+/* As xdrop_submit, but every array is DEVICE memory on the context's
+ * device and stays owned by the caller; the arrays must stay valid and
+ * unchanged until the ticket's sync returns.  n_words is the length of
+ * `packed` in words.  Pairs are validated on the device: a pair that
+ * fails the limits gets status XDROP_STATUS_INVALID and zero scores, the
+ * others are aligned, and the ticket's sync returns XDROP_EINVAL.  Results
+ * are written to `out` (device) by the time sync returns. */
+int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
+                        const uint64_t *read_off, const uint32_t *read_len,
+                        uint32_t n_reads, const xdrop_pair *pairs,
+                        size_t n_pairs, const xdrop_scoring *s,
+                        xdrop_result *out, xdrop_ticket *t);
+
+/* Wait for a ticket.  timeout_ns < 0 waits without bound; otherwise the
+ * call returns XDROP_ETIMEDOUT after about timeout_ns and the ticket stays
+ * valid for a later sync.  Returns XDROP_OK once the results are in `out`,
+ * or an error (XDROP_EINVAL for an unknown or already-synced ticket). */
+int xdrop_sync(xdrop_ctx *c, xdrop_ticket t, int64_t timeout_ns);
+
+/* Wait for all work in flight, then release every resource of c. */
+void xdrop_free(xdrop_ctx *c);
+
+/* The calling thread's last error message on c (never NULL). */
+const char *xdrop_last_error(xdrop_ctx *c);
+
+/* The CUDA stream (cudaStream_t) the context launches its work on. */
+void *xdrop_stream(xdrop_ctx *c);
+
+/* Statistics of the most recently synced ticket. */
+int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
+
+/* Cell counts: for pair p, cells[2p] and cells[2p+1] receive the number of
+ * DP cells of its left and right extension (the origin plus every cell of
+ * the anti-diagonal ranges of the reading above: the hull of the live
+ * extent of d-1 and of d-2 shifted by one, clipped to the rectangle).
+ * Inputs as xdrop_submit_device; `cells` is device memory of 2*n_pairs
+ * int64.  Synchronous.  Used to compute cell-update rates. */
+int xdrop_count_cells_device(xdrop_ctx *c, const uint32_t *packed,
+                             uint64_t n_words, const uint64_t *read_off,
+                             const uint32_t *read_len, uint32_t n_reads,
+                             const xdrop_pair *pairs, size_t n_pairs,
+                             const xdrop_scoring *s, int64_t *cells);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,643 @@
+// Host runtime of the C ABI declared in include/xdrop.h.
+//
+// A context owns one CUDA stream, a device job descriptor, scratch (task
+// order, bin counters, spill lists, the unbounded tier's diagonals) and,
+// in batched mode, one instantiated CUDA graph of the whole launch
+// sequence.  Kernels read their job descriptor from device memory, so the
+// graph is replayed unchanged for every submit (and every chunk of a
+// large submit); it is re-captured only when scratch has to grow.
+//
+// Plain mode is the paper's baseline scheme (Section "Baseline": the work
+// is split into batches of 10,000 and each is fed to the GPU in turn): one
+// launch of the 32-lane tile per 10,000-pair sub-batch, in submit order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/xdrop.h"
+#include "xd_launch.h"
+
+using namespace xd;
+
+static_assert(sizeof(xdrop_pair) == sizeof(Pair), "pair layout");
+static_assert(sizeof(xdrop_result) == 28, "result layout");
+static_assert(sizeof(xdrop_scoring) == sizeof(Scoring), "scoring layout");
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return fail(XDROP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+constexpr uint64_t kSubBatchPairs = 10000;  // plain mode (Section "Baseline")
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Counter block layout (uint32 words) in device memory.
+enum : int {
+    C_HIST = 0,          // NBINS
+    C_OFFS = 32,         // NBINS
+    C_NVALID = 64,
+    C_COUNTER = 65,
+    C_SPILL0 = 66,       // spill counts of tiers 0..2
+    C_SPILL1 = 67,
+    C_SPILL2 = 68,
+    C_NBAD = 69,
+    C_MAXLEN = 70,
+    C_WORDS = 72
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct Ticket {
+    uint64_t id = 0;
+    bool device_submit = false;
+    size_t n_pairs = 0;
+    xdrop_result *out = nullptr;  // caller's results (host submit)
+    void *d_mem = nullptr;        // inputs + results (host submit)
+    size_t d_bytes = 0;
+    void *h_pinned = nullptr;     // results staging + counters + job
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr, ev_done = nullptr;
+    uint32_t launches = 0, graph_replays = 0;
+    uint32_t *h_ctrs = nullptr;   // copy of the counter block at the end
+    Job *h_job = nullptr;
+    xdrop_result *h_out = nullptr;
+};
+
+}  // namespace
+
+struct xdrop_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    uint32_t mode = XDROP_MODE_BATCHED;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    std::unordered_map<uint64_t, Ticket *> tickets;
+    uint64_t next_id = 1;
+    size_t used = 0;  // device bytes held (scratch + tickets)
+
+    Job *d_job = nullptr;
+    uint32_t *d_ctrs = nullptr;
+    DevBuf order, spill[3], wide;
+    size_t cap_tasks = 0;
+    int64_t wide_per_cta = 0;
+    int wide_grid = 0;
+
+    // cached max read length of the last device submit
+    const uint32_t *maxlen_ptr = nullptr;
+    uint32_t maxlen_n = 0, maxlen_val = 0;
+
+    Tile tile0 = {8, 8};
+    int tile0_bps = 0;            // resident blocks per SM of tile0
+    uint64_t scratch_version = 0; // bumped whenever a scratch buffer moves
+    cudaGraphExec_t gexec = nullptr;
+    Tile graph_tile = {0, 0};
+    uint64_t graph_version = ~0ull;
+
+    xdrop_stats last = {};
+};
+
+namespace {
+
+int dev_alloc(xdrop_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (b.cap >= bytes) return XDROP_OK;
+    size_t nb = std::max(bytes, b.cap + b.cap / 2);
+    if (c->budget && c->used - b.cap + nb > c->budget) {
+        nb = bytes;
+        if (c->used - b.cap + nb > c->budget)
+            return fail(c->tickets.empty() ? XDROP_ENOMEM : XDROP_EBUSY,
+                        "device memory budget exceeded (%zu bytes needed)", nb);
+    }
+    if (b.p) {
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaFree(b.p));
+        c->used -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    CK(cudaMalloc(&b.p, nb));
+    b.cap = nb;
+    c->used += nb;
+    c->scratch_version += 1;
+    return XDROP_OK;
+}
+
+// Scratch for n_tasks tasks and the unbounded tier for reads up to maxlen.
+int ensure_scratch(xdrop_ctx *c, size_t n_tasks, uint32_t maxlen)
+{
+    size_t tasks = std::max<size_t>(n_tasks, 1024);
+    int rc;
+    if ((rc = dev_alloc(c, c->order, tasks * 4))) return rc;
+    for (auto &s : c->spill)
+        if ((rc = dev_alloc(c, s, tasks * 4))) return rc;
+    c->cap_tasks = std::min(c->order.cap, std::min(c->spill[0].cap,
+                            std::min(c->spill[1].cap, c->spill[2].cap))) / 4;
+    int64_t per = (int64_t)3 * ((int64_t)maxlen + 1);
+    per = (per + 63) / 64 * 64;
+    if (per > c->wide_per_cta) {
+        if ((rc = dev_alloc(c, c->wide, (size_t)per * 4 * c->wide_grid))) return rc;
+        c->wide_per_cta = per;
+    }
+    return XDROP_OK;
+}
+
+int validate_scoring(const xdrop_scoring *s)
+{
+    if (!s) return fail(XDROP_EINVAL, "scoring is NULL");
+    if (s->match <= 0) return fail(XDROP_EINVAL, "match must be > 0 (got %d)", s->match);
+    if (s->mismatch > 0) return fail(XDROP_EINVAL, "mismatch must be <= 0 (got %d)", s->mismatch);
+    if (s->gap >= 0) return fail(XDROP_EINVAL, "gap must be < 0 (got %d)", s->gap);
+    if (s->x < 0 || (int64_t)s->x >= LEN_LIMIT)
+        return fail(XDROP_EINVAL, "x must be in [0, 2^28) (got %d)", s->x);
+    if (s->match >= LEN_LIMIT || -(int64_t)s->mismatch >= LEN_LIMIT || -(int64_t)s->gap >= LEN_LIMIT)
+        return fail(XDROP_EINVAL, "score magnitude too large");
+    return XDROP_OK;
+}
+
+Spill spill_of(xdrop_ctx *c, int k)
+{
+    return Spill{(uint32_t *)c->spill[k].p, c->d_ctrs + C_SPILL0 + k};
+}
+
+Tile next_tile_after(Tile t)
+{
+    // The 128-wide tile for narrower first tiers, then 512.
+    if (t.width() < 128) return Tile{16, 8};
+    return Tile{32, 16};
+}
+
+// Enqueue the batched launch sequence (graph body).
+int enqueue_batched(xdrop_ctx *c, uint32_t *launches)
+{
+    cudaStream_t s = c->stream;
+    uint32_t *ctr = c->d_ctrs;
+    CK(cudaMemsetAsync(ctr, 0, C_NBAD * 4, s));  // keep NBAD / MAXLEN
+    const int bgrid = c->sm_count * 4;
+    CK(launch_binning(c->d_job, 0, bgrid, ctr + C_HIST, ctr + C_OFFS, ctr + C_NVALID,
+                      (uint32_t *)c->order.p, s));
+    const int bps = c->tile0_bps;
+    if (bps <= 0) return fail(XDROP_ECUDA, "tile %dx%d not available", c->tile0.lanes, c->tile0.c);
+    CK(launch_persistent(c->tile0, c->sm_count * bps, c->d_job, (uint32_t *)c->order.p,
+                         ctr + C_NVALID, ctr + C_COUNTER, spill_of(c, 0), s));
+    int n = 4;
+    Tile t1 = next_tile_after(c->tile0);
+    int k = 0;
+    if (t1.width() < 512) {
+        CK(launch_spill(t1, false, c->sm_count * 4, c->d_job, spill_of(c, 0), spill_of(c, 1), s));
+        k = 1;
+        ++n;
+    }
+    CK(launch_spill(Tile{32, 16}, false, c->sm_count * 2, c->d_job, spill_of(c, k),
+                    spill_of(c, k + 1), s));
+    CK(launch_wide(false, c->wide_grid, c->d_job, spill_of(c, k + 1), (int32_t *)c->wide.p,
+                   c->wide_per_cta, s));
+    n += 2;
+    if (launches) *launches = n;
+    return XDROP_OK;
+}
+
+int run_batched(xdrop_ctx *c, Ticket *tk)
+{
+    if (!c->gexec || c->graph_version != c->scratch_version ||
+        c->graph_tile.lanes != c->tile0.lanes || c->graph_tile.c != c->tile0.c) {
+        c->tile0_bps = persistent_blocks_per_sm(c->tile0);
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        uint32_t launches = 0;
+        int rc = enqueue_batched(c, &launches);
+        cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) return fail(XDROP_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(XDROP_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        c->graph_version = c->scratch_version;
+        c->graph_tile = c->tile0;
+        c->last.launches = launches;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    tk->graph_replays += 1;
+    tk->launches += c->last.launches;
+    return XDROP_OK;
+}
+
+int run_plain(xdrop_ctx *c, Ticket *tk, uint64_t n_pairs)
+{
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->d_ctrs, 0, C_NBAD * 4, s));
+    for (uint64_t p0 = 0; p0 < n_pairs; p0 += kSubBatchPairs) {
+        uint64_t np = std::min(kSubBatchPairs, n_pairs - p0);
+        CK(launch_window(Tile{32, 4}, false, c->d_job, (uint32_t)(2 * p0), (uint32_t)(2 * np),
+                         spill_of(c, 0), s));
+        tk->launches += 1;
+    }
+    CK(launch_spill(Tile{32, 16}, false, c->sm_count * 2, c->d_job, spill_of(c, 0),
+                    spill_of(c, 1), s));
+    CK(launch_wide(false, c->wide_grid, c->d_job, spill_of(c, 1), (int32_t *)c->wide.p,
+                   c->wide_per_cta, s));
+    tk->launches += 2;
+    return XDROP_OK;
+}
+
+void free_ticket(xdrop_ctx *c, Ticket *tk)
+{
+    if (tk->ev_begin) cudaEventDestroy(tk->ev_begin);
+    if (tk->ev_end) cudaEventDestroy(tk->ev_end);
+    if (tk->ev_done) cudaEventDestroy(tk->ev_done);
+    if (tk->d_mem) {
+        cudaFree(tk->d_mem);
+        c->used -= tk->d_bytes;
+    }
+    if (tk->h_pinned) cudaFreeHost(tk->h_pinned);
+    delete tk;
+}
+
+// Common tail of both submit flavours: descriptor, launches, copies back.
+int launch_ticket(xdrop_ctx *c, Ticket *tk, const Job &job, uint32_t maxlen)
+{
+    cudaStream_t s = c->stream;
+    int rc;
+    if ((rc = ensure_scratch(c, 2 * job.n_pairs, maxlen))) return rc;
+    *tk->h_job = job;
+    CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(tk->ev_begin, s));
+    if (tk->device_submit) {
+        CK(cudaMemsetAsync(c->d_ctrs + C_NBAD, 0, 4, s));
+        CK(launch_validate(c->d_job, job.n_pairs, c->d_ctrs + C_NBAD, s));
+        tk->launches += 1;
+    }
+    if (job.n_pairs) {
+        if (c->mode == XDROP_MODE_PLAIN) rc = run_plain(c, tk, job.n_pairs);
+        else rc = run_batched(c, tk);
+        if (rc) return rc;
+    }
+    CK(cudaEventRecord(tk->ev_end, s));
+    CK(cudaMemcpyAsync(tk->h_ctrs, c->d_ctrs, C_WORDS * 4, cudaMemcpyDeviceToHost, s));
+    if (!tk->device_submit && tk->n_pairs)
+        CK(cudaMemcpyAsync(tk->h_out, job.out, tk->n_pairs * sizeof(xdrop_result),
+                           cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(tk->ev_done, s));
+    return XDROP_OK;
+}
+
+int new_ticket(xdrop_ctx *c, size_t n_pairs, bool device_submit, Ticket **out)
+{
+    Ticket *tk = new Ticket();
+    tk->device_submit = device_submit;
+    tk->n_pairs = n_pairs;
+    size_t pin = align_up(sizeof(Job)) + align_up(C_WORDS * 4) +
+                 (device_submit ? 0 : align_up(n_pairs * sizeof(xdrop_result)));
+    cudaError_t e = cudaHostAlloc(&tk->h_pinned, pin, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreate(&tk->ev_begin);
+    if (e == cudaSuccess) e = cudaEventCreate(&tk->ev_end);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&tk->ev_done, cudaEventBlockingSync);
+    if (e != cudaSuccess) {
+        free_ticket(c, tk);
+        return fail(XDROP_ECUDA, "ticket setup: %s", cudaGetErrorString(e));
+    }
+    char *p = (char *)tk->h_pinned;
+    tk->h_job = (Job *)p;
+    p += align_up(sizeof(Job));
+    tk->h_ctrs = (uint32_t *)p;
+    p += align_up(C_WORDS * 4);
+    tk->h_out = device_submit ? nullptr : (xdrop_result *)p;
+    *out = tk;
+    return XDROP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xdrop_init(xdrop_ctx **out, int device, size_t budget, uint32_t flags)
+{
+    if (!out) return fail(XDROP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (flags & ~1u) return fail(XDROP_EINVAL, "unknown flags 0x%x", flags);
+    int n = 0;
+    CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(XDROP_EINVAL, "no CUDA device %d", device);
+    CK(cudaSetDevice(device));
+    xdrop_ctx *c = new xdrop_ctx();
+    c->device = device;
+    c->budget = budget;
+    c->mode = flags & 1u;
+    cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_job, sizeof(Job));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ctrs, C_WORDS * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_ctrs, 0, C_WORDS * 4);
+    if (e != cudaSuccess) {
+        xdrop_free(c);
+        return fail(XDROP_ECUDA, "init: %s", cudaGetErrorString(e));
+    }
+    c->used = sizeof(Job) + C_WORDS * 4;
+    c->wide_grid = 2 * c->sm_count;
+    *out = c;
+    return XDROP_OK;
+}
+
+int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
+                 const uint32_t *read_len, uint32_t n_reads, const xdrop_pair *pairs,
+                 size_t n_pairs, const xdrop_scoring *s, xdrop_result *out, xdrop_ticket *t)
+{
+    if (!c || !t) return fail(XDROP_EINVAL, "context or ticket pointer is NULL");
+    int rc = validate_scoring(s);
+    if (rc) return rc;
+    if (n_pairs && (!pairs || !out || !read_off || !read_len || !packed))
+        return fail(XDROP_EINVAL, "NULL input array");
+    if (2 * (uint64_t)n_pairs >= ((uint64_t)1 << 32))
+        return fail(XDROP_EINVAL, "too many pairs in one submit");
+    // Host-side validation of every read and pair.
+    uint64_t n_words = 0;
+    uint32_t maxlen = 0;
+    for (uint32_t r = 0; r < n_reads; ++r) {
+        if (read_off[r] & 15) return fail(XDROP_EINVAL, "read %u offset not a multiple of 16", r);
+        if ((int64_t)read_len[r] >= LEN_LIMIT) return fail(XDROP_EINVAL, "read %u too long", r);
+        n_words = std::max<uint64_t>(n_words, (read_off[r] + read_len[r] + 15) / 16);
+        maxlen = std::max(maxlen, read_len[r]);
+    }
+    if (n_words * 16 >= ((uint64_t)1 << 32)) return fail(XDROP_EINVAL, "packed buffer too large");
+    const Scoring sc{s->match, s->mismatch, s->gap, s->x};
+    for (size_t p = 0; p < n_pairs; ++p) {
+        const Pair &pr = *(const Pair *)&pairs[p];
+        if (!pair_ok(pr, n_reads, read_len, read_off, (int64_t)n_words, sc))
+            return fail(XDROP_EINVAL, "pair %zu is invalid (read id, seed or length limit)", p);
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    Ticket *tk = nullptr;
+    if ((rc = new_ticket(c, n_pairs, false, &tk))) return rc;
+    tk->out = out;
+    // One device allocation for the inputs and results of this ticket.
+    size_t o_packed = 0, o_off = align_up(std::max<uint64_t>(n_words, 1) * 4);
+    size_t o_len = o_off + align_up((size_t)std::max(n_reads, 1u) * 8);
+    size_t o_pairs = o_len + align_up((size_t)std::max(n_reads, 1u) * 4);
+    size_t o_out = o_pairs + align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_pair));
+    size_t bytes = o_out + align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_result));
+    if (c->budget && c->used + bytes > c->budget) {
+        free_ticket(c, tk);
+        return fail(c->tickets.empty() ? XDROP_ENOMEM : XDROP_EBUSY,
+                    "device memory budget exceeded (%zu bytes needed)", bytes);
+    }
+    cudaError_t e = cudaMalloc(&tk->d_mem, bytes);
+    if (e != cudaSuccess) {
+        free_ticket(c, tk);
+        return fail(XDROP_ECUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    tk->d_bytes = bytes;
+    c->used += bytes;
+    char *d = (char *)tk->d_mem;
+    cudaStream_t st = c->stream;
+    e = cudaSuccess;
+    if (n_words) e = cudaMemcpyAsync(d + o_packed, packed, n_words * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_reads)
+        e = cudaMemcpyAsync(d + o_off, read_off, (size_t)n_reads * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_reads)
+        e = cudaMemcpyAsync(d + o_len, read_len, (size_t)n_reads * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_pairs)
+        e = cudaMemcpyAsync(d + o_pairs, pairs, n_pairs * sizeof(xdrop_pair),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_pairs)
+        e = cudaMemsetAsync(d + o_out, 0, n_pairs * sizeof(xdrop_result), st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_ticket(c, tk);
+        return fail(XDROP_ECUDA, "input copy: %s", cudaGetErrorString(e));
+    }
+    Job job;
+    job.packed = (const uint32_t *)(d + o_packed);
+    job.n_words = (int64_t)std::max<uint64_t>(n_words, 1);
+    job.read_off = (const uint64_t *)(d + o_off);
+    job.read_len = (const uint32_t *)(d + o_len);
+    job.n_reads = n_reads;
+    job.pairs = (const Pair *)(d + o_pairs);
+    job.n_pairs = n_pairs;
+    job.sc = sc;
+    job.out = (int32_t *)(d + o_out);
+    job.cells = nullptr;
+    if ((rc = launch_ticket(c, tk, job, maxlen))) {
+        cudaStreamSynchronize(st);
+        free_ticket(c, tk);
+        return rc;
+    }
+    tk->id = c->next_id++;
+    c->tickets[tk->id] = tk;
+    *t = tk->id;
+    return XDROP_OK;
+}
+
+int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
+                        const uint64_t *read_off, const uint32_t *read_len, uint32_t n_reads,
+                        const xdrop_pair *pairs, size_t n_pairs, const xdrop_scoring *s,
+                        xdrop_result *out, xdrop_ticket *t)
+{
+    if (!c || !t) return fail(XDROP_EINVAL, "context or ticket pointer is NULL");
+    int rc = validate_scoring(s);
+    if (rc) return rc;
+    if (n_pairs && (!pairs || !out || !read_off || !read_len || !packed || !n_words))
+        return fail(XDROP_EINVAL, "NULL input array");
+    if (2 * (uint64_t)n_pairs >= ((uint64_t)1 << 32))
+        return fail(XDROP_EINVAL, "too many pairs in one submit");
+    if (n_words * 16 >= ((uint64_t)1 << 32)) return fail(XDROP_EINVAL, "packed buffer too large");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    // Largest read (sizes the unbounded tier); cached per read_len array.
+    uint32_t maxlen = c->maxlen_val;
+    if (n_pairs && (read_len != c->maxlen_ptr || n_reads != c->maxlen_n)) {
+        CK(cudaMemsetAsync(c->d_ctrs + C_MAXLEN, 0, 4, c->stream));
+        CK(launch_max_len(read_len, n_reads, c->d_ctrs + C_MAXLEN, c->stream));
+        CK(cudaMemcpyAsync(&maxlen, c->d_ctrs + C_MAXLEN, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->maxlen_ptr = read_len;
+        c->maxlen_n = n_reads;
+        c->maxlen_val = maxlen;
+    }
+    Ticket *tk = nullptr;
+    if ((rc = new_ticket(c, n_pairs, true, &tk))) return rc;
+    Job job;
+    job.packed = packed;
+    job.n_words = (int64_t)n_words;
+    job.read_off = read_off;
+    job.read_len = read_len;
+    job.n_reads = n_reads;
+    job.pairs = (const Pair *)pairs;
+    job.n_pairs = n_pairs;
+    job.sc = Scoring{s->match, s->mismatch, s->gap, s->x};
+    job.out = (int32_t *)out;
+    job.cells = nullptr;
+    if ((rc = launch_ticket(c, tk, job, maxlen))) {
+        cudaStreamSynchronize(c->stream);
+        free_ticket(c, tk);
+        return rc;
+    }
+    tk->id = c->next_id++;
+    c->tickets[tk->id] = tk;
+    *t = tk->id;
+    return XDROP_OK;
+}
+
+int xdrop_sync(xdrop_ctx *c, xdrop_ticket t, int64_t timeout_ns)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    Ticket *tk = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->tickets.find(t);
+        if (it == c->tickets.end()) return fail(XDROP_EINVAL, "unknown ticket %llu", (unsigned long long)t);
+        tk = it->second;
+    }
+    CK(cudaSetDevice(c->device));
+    if (timeout_ns < 0) {
+        CK(cudaEventSynchronize(tk->ev_done));
+    } else {
+        auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            cudaError_t q = cudaEventQuery(tk->ev_done);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return fail(XDROP_ECUDA, "sync: %s", cudaGetErrorString(q));
+            auto el = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ns) return fail(XDROP_ETIMEDOUT, "ticket %llu not done", (unsigned long long)t);
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->tickets.find(t);
+    if (it == c->tickets.end()) return fail(XDROP_EINVAL, "ticket %llu already synced", (unsigned long long)t);
+    c->tickets.erase(it);
+    if (!tk->device_submit && tk->n_pairs)
+        memcpy(tk->out, tk->h_out, tk->n_pairs * sizeof(xdrop_result));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, tk->ev_begin, tk->ev_end);
+    xdrop_stats st = {};
+    st.kernel_ms = ms;
+    st.tasks = 2 * (uint64_t)tk->n_pairs;
+    st.overflow_tasks = tk->h_ctrs[C_SPILL0];
+    st.wide_tasks = (c->mode == XDROP_MODE_PLAIN || next_tile_after(c->tile0).width() >= 512)
+                        ? tk->h_ctrs[C_SPILL1] : tk->h_ctrs[C_SPILL2];
+    st.launches = tk->launches;
+    st.graph_replays = tk->graph_replays;
+    c->last = st;
+    const uint32_t nbad = tk->device_submit ? tk->h_ctrs[C_NBAD] : 0;
+    free_ticket(c, tk);
+    if (nbad) return fail(XDROP_EINVAL, "%u pairs failed validation (status set)", nbad);
+    return XDROP_OK;
+}
+
+void xdrop_free(xdrop_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->tickets) free_ticket(c, kv.second);
+    c->tickets.clear();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    cudaFree(c->order.p);
+    for (auto &s : c->spill) cudaFree(s.p);
+    cudaFree(c->wide.p);
+    cudaFree(c->d_job);
+    cudaFree(c->d_ctrs);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *xdrop_last_error(xdrop_ctx *c)
+{
+    (void)c;
+    return g_err.c_str();
+}
+
+void *xdrop_stream(xdrop_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st)
+{
+    if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    *st = c->last;
+    return XDROP_OK;
+}
+
+int xdrop_count_cells_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
+                             const uint64_t *read_off, const uint32_t *read_len,
+                             uint32_t n_reads, const xdrop_pair *pairs, size_t n_pairs,
+                             const xdrop_scoring *s, int64_t *cells)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    int rc = validate_scoring(s);
+    if (rc) return rc;
+    if (n_pairs == 0) return XDROP_OK;
+    if (!pairs || !cells || !read_off || !read_len || !packed || !n_words)
+        return fail(XDROP_EINVAL, "NULL input array");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = c->stream;
+    CK(cudaMemsetAsync(c->d_ctrs + C_MAXLEN, 0, 4, st));
+    CK(launch_max_len(read_len, n_reads, c->d_ctrs + C_MAXLEN, st));
+    uint32_t maxlen = 0;
+    CK(cudaMemcpyAsync(&maxlen, c->d_ctrs + C_MAXLEN, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((rc = ensure_scratch(c, 2 * n_pairs, maxlen))) return rc;
+    Job job;
+    job.packed = packed;
+    job.n_words = (int64_t)n_words;
+    job.read_off = read_off;
+    job.read_len = read_len;
+    job.n_reads = n_reads;
+    job.pairs = (const Pair *)pairs;
+    job.n_pairs = n_pairs;
+    job.sc = Scoring{s->match, s->mismatch, s->gap, s->x};
+    job.out = nullptr;
+    job.cells = cells;
+    CK(cudaMemcpyAsync(c->d_job, &job, sizeof(Job), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->d_ctrs, 0, C_NBAD * 4, st));
+    CK(cudaMemsetAsync(cells, 0, 2 * n_pairs * 8, st));
+    for (uint64_t t0 = 0; t0 < 2 * n_pairs; t0 += (1u << 24)) {
+        uint32_t nt = (uint32_t)std::min<uint64_t>(1u << 24, 2 * n_pairs - t0);
+        CK(launch_window(Tile{32, 16}, true, c->d_job, (uint32_t)t0, nt, spill_of(c, 0), st));
+    }
+    CK(launch_wide(true, c->wide_grid, c->d_job, spill_of(c, 0), (int32_t *)c->wide.p,
+                   c->wide_per_cta, st));
+    CK(cudaStreamSynchronize(st));
+    return XDROP_OK;
+}
+
+}  // extern "C"

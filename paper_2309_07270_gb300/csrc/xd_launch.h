@@ -1,0 +1,45 @@
+// Host-side launchers of the device kernels (one translation unit per tile
+// family, so the library builds in parallel).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xd_types.cuh"
+
+namespace xd {
+
+struct Tile {
+    int lanes;  // lanes per extension (4, 8, 16 or 32)
+    int c;      // cells per lane per diagonal
+    int width() const { return lanes * c; }
+};
+
+// Band tiles the library is built with, narrowest first.
+constexpr int N_TILES = 7;
+extern const Tile kTiles[N_TILES];
+
+bool tile_supported(Tile t, bool persistent);
+
+// One task per group, tasks [task_base, task_base + n_tasks).
+cudaError_t launch_window(Tile t, bool count, const Job *jp, uint32_t task_base,
+                          uint32_t n_tasks, Spill spill, cudaStream_t s);
+// Persistent: positions of `order` pulled from *counter up to *n_tasks.
+cudaError_t launch_persistent(Tile t, int grid, const Job *jp, const uint32_t *order,
+                              const uint32_t *n_tasks, uint32_t *counter, Spill spill,
+                              cudaStream_t s);
+// Tasks listed in `in`, overflow to `out`.
+cudaError_t launch_spill(Tile t, bool count, int grid, const Job *jp, Spill in, Spill out,
+                         cudaStream_t s);
+// Blocks per SM of a persistent tile at 256 threads per block.
+int persistent_blocks_per_sm(Tile t);
+
+cudaError_t launch_wide(bool count, int grid, const Job *jp, Spill in, int32_t *scratch,
+                        int64_t scratch_per_cta, cudaStream_t s);
+cudaError_t launch_validate(const Job *jp, uint64_t n_pairs, uint32_t *n_bad, cudaStream_t s);
+cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *hist,
+                           uint32_t *offs, uint32_t *n_valid, uint32_t *order,
+                           cudaStream_t s);
+cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
+                           cudaStream_t s);
+
+}  // namespace xd

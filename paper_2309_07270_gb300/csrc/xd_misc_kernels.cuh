@@ -1,0 +1,118 @@
+// Non-template kernels (validation, length binning, max read length).
+// Included by exactly one translation unit.
+#pragma once
+#include "xd_device.cuh"
+
+namespace xd {
+
+// ---------------------------------------------------------------------------
+// Validation (device submits): status per pair, zero scores for bad pairs.
+// ---------------------------------------------------------------------------
+__global__ void validate_kernel(const Job *jp, uint32_t *n_bad)
+{
+    const Job J = *jp;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < J.n_pairs;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const Pair pr = J.pairs[p];
+        const bool ok = pair_ok(pr, J.n_reads, J.read_len, J.read_off, J.n_words, J.sc);
+        int32_t *o = J.out + p * 7;
+        if (!ok) {
+            for (int k = 0; k < 6; ++k) o[k] = 0;
+            o[6] = 1;
+            atomicAdd(n_bad, 1u);
+        } else {
+            o[6] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Length binning (batched form): tasks sorted into bins by
+// ceil(log2(max(m, n) + 1)), bins laid out longest first, so the persistent
+// kernel starts the longest extensions first.
+// ---------------------------------------------------------------------------
+constexpr int NBINS = 32;
+constexpr int BIN_THREADS = 256;
+
+__device__ __forceinline__ int task_bin(const Job &J, uint32_t task)
+{
+    Ext e = decode(J, task);
+    if (!e.ok) return -1;
+    uint32_t w = (uint32_t)(e.m > e.n ? e.m : e.n);
+    return 32 - __clz(w);
+}
+
+// hist[b] += tasks in bin b.  Block-local counts first, one global atomic
+// per (block, bin).
+__global__ void __launch_bounds__(BIN_THREADS)
+bin_count_kernel(const Job *jp, uint32_t *hist)
+{
+    const Job J = *jp;
+    __shared__ uint32_t h[NBINS];
+    if (threadIdx.x < NBINS) h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t n_tasks = 2 * J.n_pairs;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tasks;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        int b = task_bin(J, (uint32_t)t);
+        if (b >= 0) atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < NBINS && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// offs[b] = start of bin b in the longest-first order; *n_valid = total.
+__global__ void bin_scan_kernel(const uint32_t *hist, uint32_t *offs, uint32_t *n_valid)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = NBINS - 1; b >= 0; --b) {
+            offs[b] = run;
+            run += hist[b];
+        }
+        *n_valid = run;
+    }
+}
+
+// order[offs[b] + rank] = task.  Each block takes a contiguous range of
+// tasks, counts it per bin, reserves its slice of every bin with one
+// atomic, then places its tasks.
+__global__ void __launch_bounds__(BIN_THREADS)
+bin_scatter_kernel(const Job *jp, uint32_t *offs, uint32_t *order)
+{
+    const Job J = *jp;
+    __shared__ uint32_t h[NBINS];
+    __shared__ uint32_t base[NBINS];
+    const uint64_t n_tasks = 2 * J.n_pairs;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x; t0 < n_tasks;
+         t0 += (uint64_t)gridDim.x * blockDim.x) {
+        if (threadIdx.x < NBINS) h[threadIdx.x] = 0;
+        __syncthreads();
+        const uint64_t t = t0 + threadIdx.x;
+        int b = -1;
+        uint32_t rank = 0;
+        if (t < n_tasks) {
+            b = task_bin(J, (uint32_t)t);
+            if (b >= 0) rank = atomicAdd(&h[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < NBINS && h[threadIdx.x])
+            base[threadIdx.x] = atomicAdd(&offs[threadIdx.x], h[threadIdx.x]);
+        __syncthreads();
+        if (b >= 0) order[base[b] + rank] = (uint32_t)t;
+        __syncthreads();
+    }
+}
+
+// Largest read length (for sizing the unbounded tier's scratch).
+__global__ void max_len_kernel(const uint32_t *read_len, uint32_t n_reads, uint32_t *out)
+{
+    uint32_t m = 0;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_reads;
+         r += gridDim.x * blockDim.x)
+        m = max(m, read_len[r]);
+    m = __reduce_max_sync(FULL, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+}  // namespace xd

@@ -1,0 +1,60 @@
+// Band tiles of width 128 (X up to about 100 with unit scores); the plain
+// per-batch kernel uses the 32 x 4 tile.
+#include "xd_launch.h"
+#include "xd_device.cuh"
+
+namespace xd {
+
+template <int L, int C>
+static cudaError_t persistent_impl(int grid, const Job *jp, const uint32_t *order,
+                                   const uint32_t *n, uint32_t *ctr, Spill sp, cudaStream_t s)
+{
+    window_persistent_kernel<L, C><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
+    return cudaGetLastError();
+}
+
+template <int L, int C>
+static int occupancy_impl()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, window_persistent_kernel<L, C>, 256, 0);
+    return b;
+}
+
+cudaError_t launch_persistent_mid(Tile t, int grid, const Job *jp, const uint32_t *order,
+                                  const uint32_t *n, uint32_t *ctr, Spill sp, cudaStream_t s,
+                                  bool *handled)
+{
+    *handled = true;
+    if (t.lanes == 8 && t.c == 16) return persistent_impl<8, 16>(grid, jp, order, n, ctr, sp, s);
+    if (t.lanes == 16 && t.c == 8) return persistent_impl<16, 8>(grid, jp, order, n, ctr, sp, s);
+    if (t.lanes == 32 && t.c == 4) return persistent_impl<32, 4>(grid, jp, order, n, ctr, sp, s);
+    *handled = false;
+    return cudaSuccess;
+}
+
+int occupancy_mid(Tile t)
+{
+    if (t.lanes == 8 && t.c == 16) return occupancy_impl<8, 16>();
+    if (t.lanes == 16 && t.c == 8) return occupancy_impl<16, 8>();
+    if (t.lanes == 32 && t.c == 4) return occupancy_impl<32, 4>();
+    return -1;
+}
+
+cudaError_t launch_window_plain(const Job *jp, uint32_t task_base, uint32_t n_tasks, Spill sp,
+                                cudaStream_t s)
+{
+    const uint64_t threads = (uint64_t)n_tasks * 32;
+    const unsigned grid = (unsigned)((threads + 255) / 256);
+    if (grid == 0) return cudaSuccess;
+    window_kernel<32, 4, false><<<grid, 256, 0, s>>>(jp, task_base, n_tasks, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spill_mid(int grid, const Job *jp, Spill in, Spill out, cudaStream_t s)
+{
+    window_spill_kernel<16, 8, false><<<grid, 256, 0, s>>>(jp, in, out);
+    return cudaGetLastError();
+}
+
+}  // namespace xd

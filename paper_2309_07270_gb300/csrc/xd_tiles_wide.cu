@@ -1,0 +1,121 @@
+// Width-512 band tile (second fallback, and the cell-counting pass), the
+// unbounded tier, validation and binning.
+#include "xd_launch.h"
+#include "xd_misc_kernels.cuh"
+
+namespace xd {
+
+cudaError_t launch_spill_512(bool count, int grid, const Job *jp, Spill in, Spill out,
+                             cudaStream_t s)
+{
+    if (count) window_spill_kernel<32, 16, true><<<grid, 256, 0, s>>>(jp, in, out);
+    else window_spill_kernel<32, 16, false><<<grid, 256, 0, s>>>(jp, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_count(const Job *jp, uint32_t task_base, uint32_t n_tasks, Spill sp,
+                                cudaStream_t s)
+{
+    const uint64_t threads = (uint64_t)n_tasks * 32;
+    const unsigned grid = (unsigned)((threads + 255) / 256);
+    if (grid == 0) return cudaSuccess;
+    window_kernel<32, 16, true><<<grid, 256, 0, s>>>(jp, task_base, n_tasks, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide(bool count, int grid, const Job *jp, Spill in, int32_t *scratch,
+                        int64_t scratch_per_cta, cudaStream_t s)
+{
+    if (count) wide_kernel<true><<<grid, WIDE_THREADS, 0, s>>>(jp, in, scratch, scratch_per_cta);
+    else wide_kernel<false><<<grid, WIDE_THREADS, 0, s>>>(jp, in, scratch, scratch_per_cta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const Job *jp, uint64_t n_pairs, uint32_t *n_bad, cudaStream_t s)
+{
+    if (n_pairs == 0) return cudaSuccess;
+    uint64_t blocks = (n_pairs + 255) / 256;
+    unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
+    validate_kernel<<<grid, 256, 0, s>>>(jp, n_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *hist,
+                           uint32_t *offs, uint32_t *n_valid, uint32_t *order, cudaStream_t s)
+{
+    (void)n_pairs;
+    bin_count_kernel<<<grid, BIN_THREADS, 0, s>>>(jp, hist);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bin_scan_kernel<<<1, 32, 0, s>>>(hist, offs, n_valid);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bin_scatter_kernel<<<grid, BIN_THREADS, 0, s>>>(jp, offs, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
+                           cudaStream_t s)
+{
+    if (n_reads == 0) return cudaSuccess;
+    unsigned grid = (n_reads + 255) / 256;
+    if (grid > 1024) grid = 1024;
+    max_len_kernel<<<grid, 256, 0, s>>>(read_len, n_reads, out);
+    return cudaGetLastError();
+}
+
+// ---- dispatch over the tile families ----
+cudaError_t launch_persistent_narrow(Tile, int, const Job *, const uint32_t *, const uint32_t *,
+                                     uint32_t *, Spill, cudaStream_t, bool *);
+cudaError_t launch_persistent_mid(Tile, int, const Job *, const uint32_t *, const uint32_t *,
+                                  uint32_t *, Spill, cudaStream_t, bool *);
+int occupancy_narrow(Tile);
+int occupancy_mid(Tile);
+cudaError_t launch_window_plain(const Job *, uint32_t, uint32_t, Spill, cudaStream_t);
+cudaError_t launch_spill_mid(int, const Job *, Spill, Spill, cudaStream_t);
+
+const Tile kTiles[N_TILES] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4}, {32, 16}};
+
+bool tile_supported(Tile t, bool persistent)
+{
+    if (!persistent) return (t.lanes == 32 && (t.c == 4 || t.c == 16));
+    return occupancy_narrow(t) >= 0 || occupancy_mid(t) >= 0;
+}
+
+cudaError_t launch_window(Tile t, bool count, const Job *jp, uint32_t task_base,
+                          uint32_t n_tasks, Spill spill, cudaStream_t s)
+{
+    if (count) return launch_window_count(jp, task_base, n_tasks, spill, s);
+    if (t.lanes == 32 && t.c == 4) return launch_window_plain(jp, task_base, n_tasks, spill, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_persistent(Tile t, int grid, const Job *jp, const uint32_t *order,
+                              const uint32_t *n_tasks, uint32_t *counter, Spill spill,
+                              cudaStream_t s)
+{
+    bool handled = false;
+    cudaError_t e = launch_persistent_narrow(t, grid, jp, order, n_tasks, counter, spill, s,
+                                             &handled);
+    if (handled) return e;
+    e = launch_persistent_mid(t, grid, jp, order, n_tasks, counter, spill, s, &handled);
+    if (handled) return e;
+    return cudaErrorInvalidValue;
+}
+
+int persistent_blocks_per_sm(Tile t)
+{
+    int b = occupancy_narrow(t);
+    if (b < 0) b = occupancy_mid(t);
+    return b;
+}
+
+cudaError_t launch_spill(Tile t, bool count, int grid, const Job *jp, Spill in, Spill out,
+                         cudaStream_t s)
+{
+    if (t.lanes == 32 && t.c == 16) return launch_spill_512(count, grid, jp, in, out, s);
+    if (!count && t.lanes == 16 && t.c == 8) return launch_spill_mid(grid, jp, in, out, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace xd

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path against the oracle, element by element.
+
+Every field of every result (scores, coordinates, status) must be identical
+(integer work: bit-exact).  Cell counts from the library's counting pass
+must equal the oracle's.  Inputs are seeded synthetic workloads.
+"""
+import numpy as np
+import pytest
+
+from paper_2309_07270_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["plain", "batched"]
+
+
+@pytest.fixture(scope="module")
+def X():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_07270_gb300 import build, xdrop
+    build.build()
+    return xdrop
+
+
+@pytest.fixture(scope="module")
+def aligners(X):
+    al = {"plain": X.Aligner(mode=X.XDROP_MODE_PLAIN),
+          "batched": X.Aligner(mode=X.XDROP_MODE_BATCHED)}
+    yield al
+    for a in al.values():
+        a.close()
+
+
+def oracle_results(orc, w, x=None, nthreads=8, cells=False):
+    x = w.x if x is None else x
+    return orc.align_pairs(w.packed, w.read_off, w.read_len, w.pairs, w.match, w.mismatch,
+                           w.gap, x, nthreads=nthreads, with_cells=cells)
+
+
+def assert_same(got, want, what=""):
+    g = got.view(np.int32).reshape(-1, 7)
+    e = want.view(np.int32).reshape(-1, 7)
+    bad = np.flatnonzero((g != e).any(axis=1))
+    assert bad.size == 0, f"{what}: {bad.size} pairs differ, first {bad[:5]}: gpu {g[bad[:3]]} oracle {e[bad[:3]]}"
+
+
+def run_host(X, al, w):
+    return al.align(w.packed, w.read_off, w.read_len, w.pairs,
+                    X.scoring(w.match, w.mismatch, w.gap, w.x))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_template_pairs_200(X, aligners, orc, mode):
+    """200 template pairs, 2-4 kb, 12 % errors, X = 50, +1/-1/-1."""
+    w = W.template_pairs()
+    assert_same(run_host(X, aligners[mode], w), oracle_results(orc, w), mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("x", [0, 1, 7, 20])
+def test_tiny_and_ragged(X, aligners, orc, mode, x):
+    """Lengths 0..200 around the seed: empty extensions, ragged bands."""
+    w = W.tiny_pairs(n_pairs=300, seed=11 + x, x=x)
+    assert_same(run_host(X, aligners[mode], w), oracle_results(orc, w), f"{mode} x={x}")
+
+
+def _edge_workload(rng, x):
+    seqs_a, seqs_b, seeds = [], [], []
+    def add(a, b, sa, sb, L):
+        seqs_a.append(np.asarray(a, np.uint8)); seqs_b.append(np.asarray(b, np.uint8)); seeds.append((sa, sb, L))
+    t = rng.integers(0, 4, 3000).astype(np.uint8)
+    add(t, t, 0, 0, 17)                      # seed at both read starts
+    add(t, t, 3000 - 17, 3000 - 17, 17)      # seed at both read ends
+    add(t, t, 1500, 1500, 17)                # identical reads
+    add(t[:17], t[:17], 0, 0, 17)            # reads equal to the seed
+    add(t[:18], t[:17], 1, 0, 17)            # one base on one side
+    u = rng.integers(0, 4, 2000).astype(np.uint8)
+    v = (u + 1) & 3                          # every base mismatches
+    add(np.concatenate([u, t[:17], u]), np.concatenate([v, t[:17], v]), 2000, 2000, 17)
+    r1 = rng.integers(0, 4, 2500).astype(np.uint8)
+    r2 = rng.integers(0, 4, 1800).astype(np.uint8)
+    add(r1, r2, 700, 900, 0)                 # unrelated reads, empty seed
+    add(t, t[::-1].copy(), 100, 2000, 5)     # unrelated orientation
+    a, *_ = W.mutate(t, rng)
+    b, *_ = W.mutate(t, rng)
+    add(a, b, 0, 0, 0)                       # seedless start, related reads
+    add(a, b, len(a) - 1, len(b) - 1, 1)     # 1-base seed at the ends
+    return W.from_sequences(seqs_a, seqs_b, seeds, x=x)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("x", [0, 3, 50, 100])
+def test_edge_cases(X, aligners, orc, mode, x):
+    w = _edge_workload(np.random.default_rng(x), x)
+    assert_same(run_host(X, aligners[mode], w), oracle_results(orc, w), f"{mode} x={x}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("scores", [(2, -3, -2), (1, 0, -1), (5, -4, -3)])
+def test_other_scorings(X, aligners, orc, mode, scores):
+    w = W.template_pairs(n_pairs=40, len_lo=300, len_hi=1500, seed=4)
+    w.match, w.mismatch, w.gap = scores
+    w.x = 30
+    assert_same(run_host(X, aligners[mode], w), oracle_results(orc, w), f"{mode} {scores}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_wide_bands_use_every_tier(X, aligners, orc, mode):
+    """Large X widens the live band past the 64-, 128- and 512-slot
+    windows, so tasks spill to the wider tiers and to the unbounded one."""
+    w = W.template_pairs(n_pairs=24, len_lo=600, len_hi=1400, seed=9)
+    for x in (150, 400, 1500):
+        wx = w.with_x(x)
+        got = run_host(X, aligners[mode], wx)
+        st = aligners[mode].stats()
+        assert_same(got, oracle_results(orc, wx), f"{mode} x={x}")
+        if x >= 400:
+            assert st["overflow_tasks"] > 0
+        if x >= 1500:
+            assert st["wide_tasks"] > 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_device_submit_and_invalid_pairs(X, aligners, orc, mode):
+    w = W.template_pairs(n_pairs=64, len_lo=500, len_hi=1500, seed=12)
+    want = oracle_results(orc, w)
+    bad = w.pairs.copy()
+    bad[5]["seed_a"] = w.read_len[bad[5]["a"]]  # seed past the read end
+    bad[9]["b"] = w.n_reads + 3                 # missing read
+    dev = X.DeviceInputs(w.packed, w.read_off, w.read_len, bad)
+    al = aligners[mode]
+    with pytest.raises(X.XdropError) as ei:
+        al.align_device(dev, X.scoring(w.match, w.mismatch, w.gap, w.x))
+    assert ei.value.code == X.XDROP_EINVAL
+    got = dev.results()
+    ok = np.ones(w.n_pairs, bool)
+    ok[[5, 9]] = False
+    assert (got["status"][~ok] == X.XDROP_STATUS_INVALID).all()
+    assert (got.view(np.int32).reshape(-1, 7)[~ok, :6] == 0).all()
+    assert_same(got[ok], want[ok], mode)
+    # the host path rejects the same input before launching anything
+    out = np.zeros(w.n_pairs, X.RESULT_DTYPE)
+    with pytest.raises(X.XdropError) as ei:
+        X.xdrop_submit(al.ctx, w.packed, w.read_off, w.read_len, bad,
+                       X.scoring(1, -1, -1, 50), out)
+    assert ei.value.code == X.XDROP_EINVAL
+
+
+def test_bad_scoring_rejected(X, aligners):
+    w = W.tiny_pairs(n_pairs=4)
+    for sc in [(0, -1, -1, 5), (1, 1, -1, 5), (1, -1, 0, 5), (1, -1, -1, -1)]:
+        with pytest.raises(X.XdropError) as ei:
+            aligners["batched"].align(w.packed, w.read_off, w.read_len, w.pairs, X.scoring(*sc))
+        assert ei.value.code == X.XDROP_EINVAL
+
+
+def test_empty_submit(X, aligners):
+    w = W.tiny_pairs(n_pairs=4)
+    for al in aligners.values():
+        got = al.align(w.packed, w.read_off, w.read_len, w.pairs[:0], X.scoring())
+        assert got.shape == (0,)
+
+
+def test_cell_counts_match_oracle(X, aligners, orc):
+    w = W.template_pairs(n_pairs=60, len_lo=200, len_hi=3000, seed=13)
+    for x in (0, 20, 50, 700):
+        wx = w.with_x(x)
+        _, want = oracle_results(orc, wx, cells=True)
+        dev = X.DeviceInputs.from_workload(wx)
+        got = aligners["batched"].count_cells_device(dev, X.scoring(1, -1, -1, x)).cpu().numpy()
+        assert np.array_equal(got.reshape(-1, 2), want), f"x={x}"
+
+
+def test_modes_agree_and_repeat(X, aligners):
+    """Plain and batched forms give identical results, twice in a row."""
+    w = W.template_pairs(n_pairs=300, len_lo=200, len_hi=5000, seed=14)
+    r = [run_host(X, aligners[m], w) for m in MODES for _ in range(2)]
+    for k in range(1, 4):
+        assert np.array_equal(r[0], r[k])
+
+
+@pytest.fixture(scope="module")
+def genome29():
+    return W.genome_overlaps()
+
+
+@pytest.mark.parametrize("x", [50, 100])
+def test_genome_29x_full_size_sampled(X, aligners, orc, genome29, x):
+    """The full 29x overlap workload (about 314k pairs), batched device
+    submit as the benchmark runs it; 1200 sampled pairs against the oracle,
+    plus identical results from the host-memory submit on a slice."""
+    w = genome29.with_x(x)
+    dev = X.DeviceInputs.from_workload(w)
+    al = aligners["batched"]
+    al.align_device(dev, X.scoring(1, -1, -1, x))
+    got = dev.results()
+    assert (got["status"] == 0).all()
+    rng = np.random.default_rng(x)
+    idx = np.sort(rng.choice(w.n_pairs, 1200, replace=False))
+    want = oracle_results(orc, w.subset(idx), nthreads=16)
+    assert_same(got[idx], want, f"29x x={x}")
+    host = run_host(X, al, w.subset(np.arange(0, w.n_pairs, 97)))
+    assert np.array_equal(host, got[::97])
