@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""X-drop seed-and-extend benchmark on one GB300 (or N replicas).
+
+Workload: the 29x overlap-pair workload (uniform random 4.6 Mbp genome,
+lognormal reads of mean 10 kb / sd 6 kb, 12 % errors, every true overlap of
+at least 2 kb seeded by one exact 17-mer; about 314k pairs = 628k
+extensions), X = 50, scores +1/-1/-1, synthetic and seeded.
+
+One step = one pass of the whole alignment path over that batch through the
+C ABI: device validation and task expansion, length binning, the persistent
+band kernel, the wider fallback tiers and the result write (a CUDA graph).
+`value` is cell updates per second (GCUPS, cells counted by the reading's
+range rule) with the inputs already in HBM; `e2e` is the same metric through
+the host-memory call, with host-to-device and device-to-host copies inside
+the timed region.  The plain per-10,000-pair form is timed beside it.
+
+--impl reference times the CPU oracle (the only other implementation of
+the method here) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "X-drop GCUPS & pairs/s on 1 GB300 (bit-exact), batched vs plain; p99 @25 producers"
+UNIT = "GCUPS"
+INT_OPS_PER_CELL = 8  # algorithmic int32 ops per DP cell
+INT32_LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes, one warp instruction each per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--x", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="use only the first N pairs (small cases for profiling)")
+    ap.add_argument("--tile", default="", help="force the first tile, e.g. 8x8 (no autotune)")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(x, pairs=0):
+    import numpy as np
+    from paper_2309_07270_gb300 import workloads as W
+    w = W.genome_overlaps(seed=1, x=x)
+    if pairs and pairs < w.n_pairs:
+        w = w.subset(np.arange(pairs))
+    return w
+
+
+def workload_config(w):
+    return {"workload": "genome-29x-overlaps", "genome_bp": w.meta["genome_len"],
+            "coverage": w.meta["coverage"], "reads": w.n_reads, "pairs": w.n_pairs,
+            "extensions": 2 * w.n_pairs, "read_len_mean": w.meta["mean_len"],
+            "read_len_sd": w.meta["sd_len"], "error_rate": 0.12, "seed_len": 17,
+            "scores": [w.match, w.mismatch, w.gap], "x": w.x, "seed": w.meta["seed"]}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm (cpu_baseline, and --impl reference)
+# ---------------------------------------------------------------------------
+
+def time_oracle(w, target_s, rng_seed=0):
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(rng_seed)
+    probe = w.subset(np.sort(rng.choice(w.n_pairs, 200, replace=False)))
+    t0 = time.perf_counter()
+    _, c = oracle.align_pairs(probe.packed, probe.read_off, probe.read_len, probe.pairs,
+                              w.match, w.mismatch, w.gap, w.x, nthreads=cores, with_cells=True)
+    dt = time.perf_counter() - t0
+    per_pair = dt / 200
+    n = int(min(w.n_pairs, max(200, target_s / max(per_pair, 1e-6))))
+    idx = np.sort(rng.choice(w.n_pairs, n, replace=False))
+    s = w.subset(idx)
+    t0 = time.perf_counter()
+    _, c = oracle.align_pairs(s.packed, s.read_off, s.read_len, s.pairs, w.match, w.mismatch,
+                              w.gap, w.x, nthreads=cores, with_cells=True)
+    dt = time.perf_counter() - t0
+    cells = int(c.sum())
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} random pairs of {w.n_pairs} (seeded), {cores} threads, "
+                      f"{cells / 1e9:.2f} Gcells in {dt:.1f} s",
+            "pairs_per_s": n / dt, "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    w = workload(args.x, args.pairs)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1234)
+    per_step_pairs = 1500
+    tot_cells, tot_t, tot_pairs = 0, 0.0, 0
+    for step in range(args.warmup + args.steps):
+        per_step_pairs = min(per_step_pairs, w.n_pairs)
+        idx = np.sort(rng.choice(w.n_pairs, per_step_pairs, replace=False))
+        s = w.subset(idx)
+        t0 = time.perf_counter()
+        _, c = oracle.align_pairs(s.packed, s.read_off, s.read_len, s.pairs, w.match,
+                                  w.mismatch, w.gap, w.x, nthreads=cores, with_cells=True)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            tot_cells += int(c.sum())
+            tot_t += dt
+            tot_pairs += per_step_pairs
+    v = tot_cells / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(w),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step_pairs} random pairs per step, {cores} threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "pairs_per_s": tot_pairs / tot_t}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2309_07270_gb300", "csrc", "xd_device.cuh")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel_tag and f.get("source_sha") == sha:
+            try:
+                return float(f["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2309_07270_gb300 import build as B
+    from paper_2309_07270_gb300 import xdrop as X
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev_name = f"cuda:{local}"
+    B.build()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    w = workload(args.x, args.pairs)
+    sc = X.scoring(w.match, w.mismatch, w.gap, w.x)
+    dev = X.DeviceInputs.from_workload(w, device=dev_name)
+    batched = X.Aligner(device=local, mode=X.XDROP_MODE_BATCHED)
+    if args.tile:
+        lanes, cpl = (int(v) for v in args.tile.lower().split("x"))
+        batched.set_tile(lanes, cpl)
+    stream = torch.cuda.ExternalStream(batched.stream(), device=dev_name)
+    cells_task = batched.count_cells_device(dev, sc).cpu().numpy()
+    cells = int(cells_task.sum())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev_name)  # > 129 MB L2
+
+    def step(al, strm):
+        flush.zero_()  # L2 flush between steps, outside the timed events
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(strm)
+        t = al.submit_device(dev, sc)
+        e1.record(strm)
+        X.xdrop_sync(al.ctx, t)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), al.stats()
+
+    for _ in range(args.warmup):
+        step(batched, stream)
+    # bit-exactness spot check of the benchmarked output against the oracle
+    # lives in tests/; here the status words must all be OK.
+    res = dev.results()
+    assert (res["status"] == 0).all()
+    spills = X.xdrop_last_spills(batched.ctx)
+    cells_tier0 = cells - int(cells_task[spills].sum()) if spills.size else cells
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    step_ms, main_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        ms, st = step(batched, stream)
+        step_ms.append(ms)
+        main_ms.append(st["main_kernel_ms"])
+        launches += st["launches"]
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+
+    mean_ms = statistics.mean(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([mean_ms], device=dev_name)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        mean_ms = float(tt.item())
+    value = ws * cells / (mean_ms * 1e-3) / 1e9
+    pairs_s = ws * w.n_pairs / (mean_ms * 1e-3)
+
+    # plain per-10,000-pair form, same inputs
+    plain = None
+    if not args.no_plain:
+        pal = X.Aligner(device=local, mode=X.XDROP_MODE_PLAIN)
+        pstream = torch.cuda.ExternalStream(pal.stream(), device=dev_name)
+        for _ in range(2):
+            step(pal, pstream)
+        pms = [step(pal, pstream)[0] for _ in range(max(2, min(args.steps, 3)))]
+        assert (dev.results() == res).all()
+        pm = statistics.mean(pms)
+        plain = {"value": cells / (pm * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pm,
+                 "pairs_per_s": w.n_pairs / (pm * 1e-3), "tile": "32 lanes x 4 cells",
+                 "launch": "one launch per 10,000-pair sub-batch"}
+        pal.close()
+
+    # end to end through the host-memory call (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        def pinned(a):
+            t = torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).copy()).pin_memory()
+            return t.numpy().view(a.dtype)
+        hp, ho, hl = pinned(w.packed), pinned(w.read_off), pinned(w.read_len)
+        hpairs = pinned(w.pairs)
+        hout = torch.zeros(w.n_pairs * 28, dtype=torch.uint8).pin_memory().numpy().view(X.RESULT_DTYPE)
+        ets = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t = X.xdrop_submit(batched.ctx, hp, ho, hl, hpairs, sc, hout)
+            X.xdrop_sync(batched.ctx, t)
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                ets.append(dt)
+        assert (hout.view(np.int32) == res.view(np.int32)).all()
+        em = statistics.mean(ets)
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([em], device=dev_name)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            em = float(tt.item())
+        e2e = {"value": ws * cells / em / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(hp.nbytes + ho.nbytes + hl.nbytes + hpairs.nbytes),
+               "d2h_bytes_per_step": int(hout.nbytes), "pairs_per_s": ws * w.n_pairs / em,
+               "ms_per_step": em * 1e3, "call": "xdrop_submit + xdrop_sync (host buffers)"}
+
+    # roofline of the dominant kernel: first-tier persistent band kernel
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    main_mean = statistics.mean(main_ms) if main_ms and min(main_ms) > 0 else None
+    achieved = (INT_OPS_PER_CELL * cells_tier0 / (main_mean * 1e-3) / 1e12) if main_mean else None
+    tile = batched.tile()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tint32op/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic_from_profile(f"lockstep_kernel<{tile[0]},{tile[1]}>"),
+            "kernel": f"lockstep_kernel<{tile[0]},{tile[1]}>",
+            "kernel_ms": main_mean,
+            "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes/clk x "
+                          f"{sm_max:.0f} MHz (max SM clock)",
+            "ops_per_cell": INT_OPS_PER_CELL, "cells_in_kernel": cells_tier0,
+            "step_frac": INT_OPS_PER_CELL * cells / (mean_ms * 1e-3) / 1e12 / peak}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(w, args.cpu_seconds)
+
+    if rank == 0:
+        cfg = workload_config(w)
+        if args.pairs:
+            cfg["workload"] += f"-first-{w.n_pairs}-pairs"
+        cfg.update({"l2": "flushed between steps (256 MiB write outside the timed events)",
+                    "form": "batched: binned persistent kernel in a CUDA graph",
+                    "tile0": f"{tile[0]} lanes x {tile[1]} cells", "cells": cells,
+                    "parallelism": f"{ws} independent replica(s), no collective"})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic", "config": cfg,
+                "pairs_per_s": pairs_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "plain": plain,
+                "batched_over_plain": (value / plain["value"]) if plain else None,
+                "wall_s_timed_region": wall}
+        print(json.dumps(line), flush=True)
+    batched.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -29,8 +29,8 @@
  * buffer, which holds fewer than 2^32 bases.
  *
  * Limits (XDROP_EINVAL otherwise): match > 0, mismatch <= 0, gap < 0,
- * 0 <= x < 2^28; every |score| times (read_len[a] + read_len[b]) of a pair
- * below 2^28; read_len < 2^28; seed_a + seed_len <= read_len[a] and
+ * 0 <= x < 2^25; every |score| times (read_len[a] + read_len[b]) of a pair
+ * below 2^25; read_len < 2^28; seed_a + seed_len <= read_len[a] and
  * seed_b + seed_len <= read_len[b]; read ids < n_reads.
  *
  * Threads.  xdrop_submit* may be called from many threads at once on one
@@ -89,11 +89,17 @@ typedef struct {
 typedef struct {
     double kernel_ms;        /* device time of the last completed ticket's
                                 alignment launches (CUDA events)          */
+    double main_kernel_ms;   /* batched mode: device time of the first-tier
+                                persistent kernel alone, from events
+                                recorded inside the graph (the latest
+                                replay); 0 in plain mode                  */
     uint64_t tasks;          /* extensions (2 per pair)                   */
     uint64_t overflow_tasks; /* extensions re-run with a wider band tile  */
     uint64_t wide_tasks;     /* extensions that needed the unbounded tier */
     uint32_t launches;       /* kernel launches of that ticket            */
     uint32_t graph_replays;  /* CUDA graph launches of that ticket        */
+    uint32_t tile_lanes;     /* first band tier: lanes per extension      */
+    uint32_t tile_cells;     /* first band tier: cells per lane           */
 } xdrop_stats;
 
 /* Create a context on CUDA device `device`.  device_mem_budget bounds the
@@ -145,6 +151,21 @@ void *xdrop_stream(xdrop_ctx *c);
 
 /* Statistics of the most recently synced ticket. */
 int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
+
+/* Batched mode: fix the first band tier to `lanes` lanes per extension
+ * and `cells` cells per lane (lanes*cells slots per anti-diagonal parity),
+ * or pass lanes = 0 to go back to autotuning.  Autotuning (the default)
+ * times every first-tier tile on a sample of the first submit with a new
+ * scoring and keeps the fastest for that scoring.  Tiles: 4x16, 8x8, 16x4,
+ * 8x16, 16x8, 32x4.  Returns XDROP_EINVAL for another shape. */
+int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells);
+
+/* Task ids (2*pair + 1 for a right extension, 2*pair for a left one)
+ * that the first band tier handed to a wider tier during the most recently
+ * synced ticket.  Copies up to cap ids to dst (host memory) and the total
+ * number to *n.  For diagnostics and for separating the first tier's work
+ * in rate measurements. */
+int xdrop_last_spills(xdrop_ctx *c, uint32_t *dst, size_t cap, size_t *n);
 
 /* Cell counts: for pair p, cells[2p] and cells[2p+1] receive the number of
  * DP cells of its left and right extension (the origin plus every cell of

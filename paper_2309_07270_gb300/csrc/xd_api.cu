@@ -17,7 +17,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -119,8 +121,11 @@ struct xdrop_ctx {
 
     Tile tile0 = {8, 8};
     int tile0_bps = 0;            // resident blocks per SM of tile0
+    Tile forced = {0, 0};         // xdrop_set_tile
+    std::map<std::tuple<int, int, int, int>, Tile> tuned;  // per scoring
     uint64_t scratch_version = 0; // bumped whenever a scratch buffer moves
     cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev_main0 = nullptr, ev_main1 = nullptr;  // recorded inside the graph
     Tile graph_tile = {0, 0};
     uint64_t graph_version = ~0ull;
 
@@ -178,9 +183,9 @@ int validate_scoring(const xdrop_scoring *s)
     if (s->match <= 0) return fail(XDROP_EINVAL, "match must be > 0 (got %d)", s->match);
     if (s->mismatch > 0) return fail(XDROP_EINVAL, "mismatch must be <= 0 (got %d)", s->mismatch);
     if (s->gap >= 0) return fail(XDROP_EINVAL, "gap must be < 0 (got %d)", s->gap);
-    if (s->x < 0 || (int64_t)s->x >= LEN_LIMIT)
-        return fail(XDROP_EINVAL, "x must be in [0, 2^28) (got %d)", s->x);
-    if (s->match >= LEN_LIMIT || -(int64_t)s->mismatch >= LEN_LIMIT || -(int64_t)s->gap >= LEN_LIMIT)
+    if (s->x < 0 || (int64_t)s->x >= SCORE_LIMIT)
+        return fail(XDROP_EINVAL, "x must be in [0, 2^25) (got %d)", s->x);
+    if (s->match >= SCORE_LIMIT || -(int64_t)s->mismatch >= SCORE_LIMIT || -(int64_t)s->gap >= SCORE_LIMIT)
         return fail(XDROP_EINVAL, "score magnitude too large");
     return XDROP_OK;
 }
@@ -197,8 +202,8 @@ Tile next_tile_after(Tile t)
     return Tile{32, 16};
 }
 
-// Enqueue the batched launch sequence (graph body).
-int enqueue_batched(xdrop_ctx *c, uint32_t *launches)
+// Enqueue the batched launch sequence (graph body) with first tile t0.
+int enqueue_batched(xdrop_ctx *c, Tile t0, int bps, bool main_events, uint32_t *launches)
 {
     cudaStream_t s = c->stream;
     uint32_t *ctr = c->d_ctrs;
@@ -206,12 +211,14 @@ int enqueue_batched(xdrop_ctx *c, uint32_t *launches)
     const int bgrid = c->sm_count * 4;
     CK(launch_binning(c->d_job, 0, bgrid, ctr + C_HIST, ctr + C_OFFS, ctr + C_NVALID,
                       (uint32_t *)c->order.p, s));
-    const int bps = c->tile0_bps;
-    if (bps <= 0) return fail(XDROP_ECUDA, "tile %dx%d not available", c->tile0.lanes, c->tile0.c);
-    CK(launch_persistent(c->tile0, c->sm_count * bps, c->d_job, (uint32_t *)c->order.p,
+    if (bps <= 0) return fail(XDROP_ECUDA, "tile %dx%d not available", t0.lanes, t0.c);
+    // External record nodes, so the events are really recorded on replay.
+    if (main_events) CK(cudaEventRecordWithFlags(c->ev_main0, s, cudaEventRecordExternal));
+    CK(launch_persistent(t0, c->sm_count * bps, c->d_job, (uint32_t *)c->order.p,
                          ctr + C_NVALID, ctr + C_COUNTER, spill_of(c, 0), s));
+    if (main_events) CK(cudaEventRecordWithFlags(c->ev_main1, s, cudaEventRecordExternal));
     int n = 4;
-    Tile t1 = next_tile_after(c->tile0);
+    Tile t1 = next_tile_after(t0);
     int k = 0;
     if (t1.width() < 512) {
         CK(launch_spill(t1, false, c->sm_count * 4, c->d_job, spill_of(c, 0), spill_of(c, 1), s));
@@ -227,6 +234,49 @@ int enqueue_batched(xdrop_ctx *c, uint32_t *launches)
     return XDROP_OK;
 }
 
+// Candidate first tiles for autotuning (all persistent instantiations).
+const Tile kTuneTiles[] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4}};
+
+// Time the whole batched sequence for every candidate first tile on a
+// sample of `job` (its first pairs), pick the fastest.  Synchronous.
+int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
+{
+    cudaStream_t s = c->stream;
+    Job js = job;
+    js.n_pairs = std::min<uint64_t>(job.n_pairs, std::max<uint64_t>(4096, job.n_pairs / 8));
+    CK(cudaStreamSynchronize(s));
+    *tk->h_job = js;
+    CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = Tile{0, 0};
+    for (const Tile &t : kTuneTiles) {
+        const int bps = persistent_blocks_per_sm(t);
+        if (bps <= 0) continue;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, s));
+            int rc = enqueue_batched(c, t, bps, false, nullptr);
+            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tmin = std::min(tmin, ms);
+        }
+        if (tmin < best_ms) { best_ms = tmin; *best = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the full job for the real run
+    *tk->h_job = job;
+    CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return best->lanes ? XDROP_OK : fail(XDROP_ECUDA, "no tile could be timed");
+}
+
 int run_batched(xdrop_ctx *c, Ticket *tk)
 {
     if (!c->gexec || c->graph_version != c->scratch_version ||
@@ -239,7 +289,7 @@ int run_batched(xdrop_ctx *c, Ticket *tk)
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         uint32_t launches = 0;
-        int rc = enqueue_batched(c, &launches);
+        int rc = enqueue_batched(c, c->tile0, c->tile0_bps, true, &launches);
         cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
@@ -304,6 +354,20 @@ int launch_ticket(xdrop_ctx *c, Ticket *tk, const Job &job, uint32_t maxlen)
         CK(launch_validate(c->d_job, job.n_pairs, c->d_ctrs + C_NBAD, s));
         tk->launches += 1;
     }
+    if (job.n_pairs && c->mode != XDROP_MODE_PLAIN) {
+        Tile t = c->forced;
+        if (!t.lanes) {
+            auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x);
+            auto it = c->tuned.find(key);
+            if (it == c->tuned.end()) {
+                if ((rc = autotune(c, tk, job, &t))) return rc;
+                c->tuned[key] = t;
+            } else {
+                t = it->second;
+            }
+        }
+        c->tile0 = t;
+    }
     if (job.n_pairs) {
         if (c->mode == XDROP_MODE_PLAIN) rc = run_plain(c, tk, job.n_pairs);
         else rc = run_batched(c, tk);
@@ -365,6 +429,8 @@ int xdrop_init(xdrop_ctx **out, int device, size_t budget, uint32_t flags)
     if (e == cudaSuccess) e = cudaMalloc(&c->d_job, sizeof(Job));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ctrs, C_WORDS * 4);
     if (e == cudaSuccess) e = cudaMemset(c->d_ctrs, 0, C_WORDS * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_main0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_main1);
     if (e != cudaSuccess) {
         xdrop_free(c);
         return fail(XDROP_ECUDA, "init: %s", cudaGetErrorString(e));
@@ -546,16 +612,22 @@ int xdrop_sync(xdrop_ctx *c, xdrop_ticket t, int64_t timeout_ns)
     c->tickets.erase(it);
     if (!tk->device_submit && tk->n_pairs)
         memcpy(tk->out, tk->h_out, tk->n_pairs * sizeof(xdrop_result));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, tk->ev_begin, tk->ev_end);
+    float ms = 0.f, ms_main = 0.f;
+    if (cudaEventElapsedTime(&ms, tk->ev_begin, tk->ev_end) != cudaSuccess) ms = 0.f;
+    if (tk->graph_replays && cudaEventElapsedTime(&ms_main, c->ev_main0, c->ev_main1) != cudaSuccess)
+        ms_main = 0.f;
+    (void)cudaGetLastError();  // a failed timing query must not leak into later checks
     xdrop_stats st = {};
     st.kernel_ms = ms;
+    st.main_kernel_ms = ms_main;
     st.tasks = 2 * (uint64_t)tk->n_pairs;
     st.overflow_tasks = tk->h_ctrs[C_SPILL0];
     st.wide_tasks = (c->mode == XDROP_MODE_PLAIN || next_tile_after(c->tile0).width() >= 512)
                         ? tk->h_ctrs[C_SPILL1] : tk->h_ctrs[C_SPILL2];
     st.launches = tk->launches;
     st.graph_replays = tk->graph_replays;
+    st.tile_lanes = c->mode == XDROP_MODE_PLAIN ? 32 : c->tile0.lanes;
+    st.tile_cells = c->mode == XDROP_MODE_PLAIN ? 4 : c->tile0.c;
     c->last = st;
     const uint32_t nbad = tk->device_submit ? tk->h_ctrs[C_NBAD] : 0;
     free_ticket(c, tk);
@@ -571,6 +643,8 @@ void xdrop_free(xdrop_ctx *c)
     for (auto &kv : c->tickets) free_ticket(c, kv.second);
     c->tickets.clear();
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->ev_main0) cudaEventDestroy(c->ev_main0);
+    if (c->ev_main1) cudaEventDestroy(c->ev_main1);
     cudaFree(c->order.p);
     for (auto &s : c->spill) cudaFree(s.p);
     cudaFree(c->wide.p);
@@ -593,6 +667,36 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st)
     if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
     *st = c->last;
+    return XDROP_OK;
+}
+
+int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (lanes == 0) {
+        c->forced = Tile{0, 0};
+        return XDROP_OK;
+    }
+    for (const Tile &t : kTuneTiles)
+        if (t.lanes == lanes && t.c == cells) {
+            c->forced = t;
+            return XDROP_OK;
+        }
+    return fail(XDROP_EINVAL, "no %dx%d tile", lanes, cells);
+}
+
+int xdrop_last_spills(xdrop_ctx *c, uint32_t *dst, size_t cap, size_t *n)
+{
+    if (!c || !n || (cap && !dst)) return fail(XDROP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    uint32_t cnt = 0;
+    CK(cudaMemcpy(&cnt, c->d_ctrs + C_SPILL0, 4, cudaMemcpyDeviceToHost));
+    *n = cnt;
+    size_t k = std::min<size_t>(cap, cnt);
+    if (k) CK(cudaMemcpy(dst, c->spill[0].p, k * 4, cudaMemcpyDeviceToHost));
     return XDROP_OK;
 }
 

@@ -415,6 +415,282 @@ window_spill_kernel(const Job *jp, Spill in, Spill out)
 }
 
 // ---------------------------------------------------------------------------
+// Lockstep band kernel: 32/L extensions per warp that step their
+// anti-diagonals together.
+//
+// Groups of a warp stay convergent: every per-group decision is either
+// predicated (best-cell update, termination) or taken under a warp-wide
+// vote (masked cells near the rectangle's far edges, window shifts, base
+// refills, task switches), so the warp never splits into groups that issue
+// separately.  New tasks start only at the top of an odd diagonal, so all
+// groups share the diagonal parity.  The lane maximum runs over packed keys
+// value*16 + (15 - t): the group maximum of the keys gives both the best
+// value and, with one ballot, the first (smallest i) cell holding it.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t ld_word_u(const uint32_t *pk, int64_t nw, int64_t w)
+{
+    w = w < 0 ? 0 : (w >= nw ? nw - 1 : w);
+    return __ldg(pk + w);
+}
+
+__device__ __forceinline__ uint32_t load16_u(const uint32_t *pk, int64_t nw, int64_t q)
+{
+    const int64_t w = q >> 4;
+    const uint32_t sh = (uint32_t)(q & 15) * 2u;
+    return __funnelshift_r(ld_word_u(pk, nw, w), ld_word_u(pk, nw, w + 1), sh);
+}
+
+// field u = c_{k+u} of the stream c_k = base s0 + dir*(k-1)
+__device__ __forceinline__ uint32_t fwd16_u(const uint32_t *pk, int64_t nw, int64_t s0, int dir,
+                                            int32_t k)
+{
+    if (dir > 0) return load16_u(pk, nw, s0 + (k - 1));
+    return rev16(load16_u(pk, nw, s0 - (k - 1) - 15));
+}
+
+// field t = c_{k-t}
+__device__ __forceinline__ uint32_t back16_u(const uint32_t *pk, int64_t nw, int64_t s0, int dir,
+                                             int32_t k)
+{
+    if (dir > 0) return rev16(load16_u(pk, nw, s0 + (k - 16)));
+    return load16_u(pk, nw, s0 - (k - 1));
+}
+
+template <int C, bool ODD, bool MASKED>
+__device__ __forceinline__ int32_t dp_step_key(int32_t (&V)[C], const int32_t (&U)[C],
+                                               int32_t edge, uint32_t eq, const Scoring &sc,
+                                               int32_t thr, int32_t i0, int32_t j0, int32_t m,
+                                               int32_t n)
+{
+    int32_t lkey = NEG * 16;
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+        int32_t nb;
+        if (ODD) nb = imax(U[t], (t + 1 < C) ? U[t + 1] : edge);
+        else nb = imax((t > 0) ? U[t - 1] : edge, U[t]);
+        const int32_t s = ((eq >> (2 * t)) & 1u) ? sc.match : sc.mismatch;
+        int32_t r = imax(V[t] + s, nb + sc.gap);
+        if (MASKED) {
+            if (i0 + t > m || j0 - t > n) r = NEG;
+        }
+        r = (r >= thr) ? r : NEG;
+        V[t] = r;
+        lkey = imax(lkey, r * 16 + (15 - t));
+    }
+    return lkey;
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(256)
+lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_ptr,
+                uint32_t *counter, Spill spill)
+{
+    static_assert(C <= 16 && 32 % L == 0, "tile shape");
+    constexpr int W = L * C;
+    const Job J = *jp;
+    const Scoring sc = J.sc;
+    const uint32_t *pk = J.packed;
+    const int64_t nw = J.n_words;
+    const int lane = threadIdx.x & 31;
+    const int glane = lane % L;
+    const int gbase = lane - glane;
+    const unsigned gm = group_mask<L>(gbase);
+    const uint32_t n_tasks = *n_tasks_ptr;
+
+    // Per-group task state (uniform within a group).
+    bool active = false, exhausted = false;
+    uint32_t task = 0;
+    int64_t sa0 = 0, sb0 = 0;  // stream anchors of a and b
+    int dir = 1;
+    int32_t m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
+    bool prev_dead = false;
+    int32_t E[C], O[C];
+#pragma unroll
+    for (int t = 0; t < C; ++t) { E[t] = NEG; O[t] = NEG; }
+    uint32_t Aw = 0, LA = 0, Bw = 0, LB = 0;
+    int la_n = 16, lb_n = 16;  // warp-uniform lookahead counters
+
+    // End of a task: result (or hand-off to the next tier) by the leader.
+    auto retire = [&](bool overflow) {
+        if (glane == 0) {
+            if (overflow) {
+                const uint32_t q = atomicAdd(spill.count, 1u);
+                spill.list[q] = task;
+            } else {
+                const Pair p = J.pairs[task >> 1];
+                int32_t *o = J.out + (size_t)(task >> 1) * 7;
+                if (task & 1u) {
+                    o[3] = T;
+                    o[4] = (int32_t)(p.seed_a + p.seed_len) + bi;
+                    o[5] = (int32_t)(p.seed_b + p.seed_len) + bj;
+                } else {
+                    o[0] = T;
+                    o[1] = (int32_t)p.seed_a - bi;
+                    o[2] = (int32_t)p.seed_b - bj;
+                }
+            }
+        }
+        active = false;
+    };
+
+    // Bookkeeping after diagonal d (V holds it, U the other parity).
+    auto finish = [&](int32_t (&V)[C], int32_t lkey, const bool odd) {
+        // The key orders cells within a lane only: take the lowest lane
+        // whose maximum is M, then that lane's first cell holding it.
+        const int32_t mkey = __reduce_max_sync(gm, lkey);
+        const int32_t M = mkey >> 4;
+        const unsigned hits = __ballot_sync(FULL, (lkey >> 4) == M) & gm;
+        const int src = __ffs(hits) - 1;
+        const int32_t skey = __shfl_sync(FULL, lkey, src);
+        if (active && M > T) {
+            bi = (i0 - glane * C) + (src - gbase) * C + (15 - (skey & 15));
+            bj = d - bi;
+            T = M;
+        }
+        const bool dead = (M == NEG);
+        bool fin = active && ((dead && prev_dead) || d >= m + n);
+        prev_dead = dead;
+        // Window edges: after an odd diagonal the top slot may seed a cell
+        // above the window, after an even one the bottom slot one below it.
+        const int32_t vedge = odd ? __shfl_sync(FULL, V[C - 1], L - 1, L)
+                                  : __shfl_sync(FULL, V[0], 0, L);
+        const bool want = active && !fin && vedge != NEG;
+        bool ovf = false;
+        if (__any_sync(FULL, want)) {
+            const int32_t vopp = odd ? __shfl_sync(FULL, V[0], 0, L)
+                                     : __shfl_sync(FULL, V[C - 1], L - 1, L);
+            ovf = want && vopp != NEG;
+            const bool sh = want && !ovf;
+            if (odd) {  // shift up: slot s takes slot s+1
+                int32_t ne = __shfl_down_sync(FULL, E[0], 1, L);
+                int32_t no = __shfl_down_sync(FULL, O[0], 1, L);
+                if (glane == L - 1) { ne = NEG; no = NEG; }
+                if (sh) {
+#pragma unroll
+                    for (int t = 0; t < C - 1; ++t) { E[t] = E[t + 1]; O[t] = O[t + 1]; }
+                    E[C - 1] = ne;
+                    O[C - 1] = no;
+                    i0 += 1;
+                    j0 -= 1;
+                }
+            } else {    // shift down: slot s takes slot s-1
+                int32_t pe = __shfl_up_sync(FULL, E[C - 1], 1, L);
+                int32_t po = __shfl_up_sync(FULL, O[C - 1], 1, L);
+                if (glane == 0) { pe = NEG; po = NEG; }
+                if (sh) {
+#pragma unroll
+                    for (int t = C - 1; t > 0; --t) { E[t] = E[t - 1]; O[t] = O[t - 1]; }
+                    E[0] = pe;
+                    O[0] = po;
+                    i0 -= 1;
+                    j0 += 1;
+                }
+            }
+            if (sh) {
+                Aw = fwd16_u(pk, nw, sa0, dir, i0);
+                LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+                Bw = back16_u(pk, nw, sb0, dir, j0);
+                LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+            }
+            fin = fin || ovf;
+        }
+        if (fin) retire(ovf);
+    };
+
+    for (;;) {
+        // ---------------- task switches (top of an odd diagonal) ----------------
+        const bool need = !active && !exhausted;
+        if (__any_sync(FULL, need)) {
+            if (need) {
+                uint32_t q = 0;
+                if (glane == 0) q = atomicAdd(counter, 1u);
+                q = __shfl_sync(gm, q, gbase);
+                if (q >= n_tasks) {
+                    exhausted = true;
+                } else {
+                    task = order ? order[q] : q;
+                    const Ext e = decode(J, task);
+                    if (e.ok) {
+                        sa0 = e.A.s0;
+                        sb0 = e.B.s0;
+                        dir = e.A.dir;
+                        m = e.m;
+                        n = e.n;
+#pragma unroll
+                        for (int t = 0; t < C; ++t) {
+                            E[t] = (glane * C + t == W / 2) ? 0 : NEG;  // origin at k = 0
+                            O[t] = NEG;
+                        }
+                        i0 = -(W / 2) + glane * C;
+                        j0 = (W / 2) - glane * C;
+                        Aw = fwd16_u(pk, nw, sa0, dir, i0);
+                        LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+                        Bw = back16_u(pk, nw, sb0, dir, j0);
+                        LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+                        d = 0;
+                        T = 0;
+                        bi = 0;
+                        bj = 0;
+                        prev_dead = false;
+                        active = true;
+                    }
+                }
+            }
+        }
+        if (__all_sync(FULL, exhausted && !active)) break;
+        if (!__any_sync(FULL, active)) continue;
+
+        // ---------------- odd diagonal: a-window advances ----------------
+        ++d;
+        ++i0;
+        Aw = __funnelshift_r(Aw, LA, 2);
+        LA >>= 2;
+        if (--la_n == 0) {
+            LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+            la_n = 16;
+        }
+        {
+            const int32_t thr = T - sc.x;
+            const uint32_t xx = Aw ^ Bw;
+            const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
+            int32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
+            if (glane == L - 1) edge = NEG;
+            const bool nm = active && ((i0 - glane * C + W - 1 > m) || (j0 + glane * C > n));
+            int32_t lkey;
+            if (__any_sync(FULL, nm))
+                lkey = dp_step_key<C, true, true>(O, E, edge, eq, sc, thr, i0, j0, m, n);
+            else
+                lkey = dp_step_key<C, true, false>(O, E, edge, eq, sc, thr, i0, j0, m, n);
+            finish(O, lkey, true);
+        }
+        // ---------------- even diagonal: b-window advances ----------------
+        ++d;
+        ++j0;
+        Bw = __funnelshift_l(LB, Bw, 2);
+        LB <<= 2;
+        if (--lb_n == 0) {
+            LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+            lb_n = 16;
+        }
+        {
+            const int32_t thr = T - sc.x;
+            const uint32_t xx = Aw ^ Bw;
+            const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
+            int32_t edge = __shfl_up_sync(FULL, O[C - 1], 1, L);
+            if (glane == 0) edge = NEG;
+            const bool nm = active && ((i0 - glane * C + W - 1 > m) || (j0 + glane * C > n));
+            int32_t lkey;
+            if (__any_sync(FULL, nm))
+                lkey = dp_step_key<C, false, true>(E, O, edge, eq, sc, thr, i0, j0, m, n);
+            else
+                lkey = dp_step_key<C, false, false>(E, O, edge, eq, sc, thr, i0, j0, m, n);
+            finish(E, lkey, false);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Unbounded tier: one CTA per extension, step-4 ranges, global scratch.
 // ---------------------------------------------------------------------------
 constexpr int WIDE_THREADS = 256;

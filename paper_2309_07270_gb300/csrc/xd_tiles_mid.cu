@@ -9,7 +9,8 @@ template <int L, int C>
 static cudaError_t persistent_impl(int grid, const Job *jp, const uint32_t *order,
                                    const uint32_t *n, uint32_t *ctr, Spill sp, cudaStream_t s)
 {
-    window_persistent_kernel<L, C><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
+    (void)cudaGetLastError();
+    lockstep_kernel<L, C><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
     return cudaGetLastError();
 }
 
@@ -17,7 +18,7 @@ template <int L, int C>
 static int occupancy_impl()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, window_persistent_kernel<L, C>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lockstep_kernel<L, C>, 256, 0);
     return b;
 }
 
@@ -47,12 +48,14 @@ cudaError_t launch_window_plain(const Job *jp, uint32_t task_base, uint32_t n_ta
     const uint64_t threads = (uint64_t)n_tasks * 32;
     const unsigned grid = (unsigned)((threads + 255) / 256);
     if (grid == 0) return cudaSuccess;
+    (void)cudaGetLastError();
     window_kernel<32, 4, false><<<grid, 256, 0, s>>>(jp, task_base, n_tasks, sp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spill_mid(int grid, const Job *jp, Spill in, Spill out, cudaStream_t s)
 {
+    (void)cudaGetLastError();
     window_spill_kernel<16, 8, false><<<grid, 256, 0, s>>>(jp, in, out);
     return cudaGetLastError();
 }

@@ -8,7 +8,8 @@ template <int L, int C>
 static cudaError_t persistent_impl(int grid, const Job *jp, const uint32_t *order,
                                    const uint32_t *n, uint32_t *ctr, Spill sp, cudaStream_t s)
 {
-    window_persistent_kernel<L, C><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
+    (void)cudaGetLastError();
+    lockstep_kernel<L, C><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
     return cudaGetLastError();
 }
 
@@ -16,7 +17,7 @@ template <int L, int C>
 static int occupancy_impl()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, window_persistent_kernel<L, C>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lockstep_kernel<L, C>, 256, 0);
     return b;
 }
 

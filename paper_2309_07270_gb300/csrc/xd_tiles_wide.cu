@@ -8,6 +8,7 @@ namespace xd {
 cudaError_t launch_spill_512(bool count, int grid, const Job *jp, Spill in, Spill out,
                              cudaStream_t s)
 {
+    (void)cudaGetLastError();
     if (count) window_spill_kernel<32, 16, true><<<grid, 256, 0, s>>>(jp, in, out);
     else window_spill_kernel<32, 16, false><<<grid, 256, 0, s>>>(jp, in, out);
     return cudaGetLastError();
@@ -19,6 +20,7 @@ cudaError_t launch_window_count(const Job *jp, uint32_t task_base, uint32_t n_ta
     const uint64_t threads = (uint64_t)n_tasks * 32;
     const unsigned grid = (unsigned)((threads + 255) / 256);
     if (grid == 0) return cudaSuccess;
+    (void)cudaGetLastError();
     window_kernel<32, 16, true><<<grid, 256, 0, s>>>(jp, task_base, n_tasks, sp);
     return cudaGetLastError();
 }
@@ -26,6 +28,7 @@ cudaError_t launch_window_count(const Job *jp, uint32_t task_base, uint32_t n_ta
 cudaError_t launch_wide(bool count, int grid, const Job *jp, Spill in, int32_t *scratch,
                         int64_t scratch_per_cta, cudaStream_t s)
 {
+    (void)cudaGetLastError();
     if (count) wide_kernel<true><<<grid, WIDE_THREADS, 0, s>>>(jp, in, scratch, scratch_per_cta);
     else wide_kernel<false><<<grid, WIDE_THREADS, 0, s>>>(jp, in, scratch, scratch_per_cta);
     return cudaGetLastError();
@@ -36,6 +39,7 @@ cudaError_t launch_validate(const Job *jp, uint64_t n_pairs, uint32_t *n_bad, cu
     if (n_pairs == 0) return cudaSuccess;
     uint64_t blocks = (n_pairs + 255) / 256;
     unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
+    (void)cudaGetLastError();
     validate_kernel<<<grid, 256, 0, s>>>(jp, n_bad);
     return cudaGetLastError();
 }
@@ -44,6 +48,7 @@ cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *
                            uint32_t *offs, uint32_t *n_valid, uint32_t *order, cudaStream_t s)
 {
     (void)n_pairs;
+    (void)cudaGetLastError();
     bin_count_kernel<<<grid, BIN_THREADS, 0, s>>>(jp, hist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -60,6 +65,7 @@ cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t 
     if (n_reads == 0) return cudaSuccess;
     unsigned grid = (n_reads + 255) / 256;
     if (grid > 1024) grid = 1024;
+    (void)cudaGetLastError();
     max_len_kernel<<<grid, 256, 0, s>>>(read_len, n_reads, out);
     return cudaGetLastError();
 }

@@ -6,7 +6,10 @@
 
 namespace xd {
 
-constexpr int32_t NEG = -(1 << 30);  // pruned cell; thresholds stay > NEG
+// Pruned cell.  Every threshold T - x is >= -x > -2^25 > NEG, and any
+// live or pruned value times 16 plus 15 still fits in int32 (the packed
+// best-cell key of the lockstep kernels).
+constexpr int32_t NEG = -(1 << 26);
 constexpr uint32_t FULL = 0xffffffffu;
 
 struct Pair {
@@ -59,7 +62,8 @@ struct Ext {
 // ---------------------------------------------------------------------------
 // Limits (also enforced on the host for host submits).
 // ---------------------------------------------------------------------------
-constexpr int64_t LEN_LIMIT = (int64_t)1 << 28;
+constexpr int64_t LEN_LIMIT = (int64_t)1 << 28;    // read length
+constexpr int64_t SCORE_LIMIT = (int64_t)1 << 25;  // |score| * (len_a + len_b), and x
 
 __host__ __device__ inline int32_t max_abs_score(const Scoring &s)
 {
@@ -80,7 +84,7 @@ __host__ __device__ inline bool pair_ok(const Pair &p, uint32_t n_reads,
     if ((int64_t)la >= LEN_LIMIT || (int64_t)lb >= LEN_LIMIT) return false;
     if ((uint64_t)p.seed_a + p.seed_len > la) return false;
     if ((uint64_t)p.seed_b + p.seed_len > lb) return false;
-    if ((int64_t)(la + lb) * max_abs_score(s) >= LEN_LIMIT) return false;
+    if ((int64_t)(la + lb) * max_abs_score(s) >= SCORE_LIMIT) return false;
     uint64_t oa = read_off[p.a], ob = read_off[p.b];
     if ((oa & 15) || (ob & 15)) return false;
     if ((int64_t)((oa + la + 15) / 16) > n_words) return false;

@@ -35,7 +35,7 @@ RESULT_DTYPE = np.dtype([("left_score", "<i4"), ("left_begin_a", "<i4"),
 
 EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_free", "xdrop_last_error", "xdrop_stream", "xdrop_get_stats",
-           "xdrop_count_cells_device"]
+           "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile"]
 
 
 class XdropError(RuntimeError):
@@ -50,9 +50,11 @@ class Scoring(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("kernel_ms", ctypes.c_double), ("tasks", ctypes.c_uint64),
+    _fields_ = [("kernel_ms", ctypes.c_double), ("main_kernel_ms", ctypes.c_double),
+                ("tasks", ctypes.c_uint64),
                 ("overflow_tasks", ctypes.c_uint64), ("wide_tasks", ctypes.c_uint64),
-                ("launches", ctypes.c_uint32), ("graph_replays", ctypes.c_uint32)]
+                ("launches", ctypes.c_uint32), ("graph_replays", ctypes.c_uint32),
+                ("tile_lanes", ctypes.c_uint32), ("tile_cells", ctypes.c_uint32)]
 
 
 _lib = None
@@ -83,7 +85,9 @@ def load():
     lib.xdrop_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.xdrop_count_cells_device.argtypes = [vp, vp, u64, vp, vp, u32, vp, sz,
                                              ctypes.POINTER(Scoring), vp]
-    for name in ("xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
+    lib.xdrop_last_spills.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
+    lib.xdrop_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    for name in ("xdrop_set_tile", "xdrop_last_spills", "xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
                  "xdrop_get_stats", "xdrop_count_cells_device"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -171,6 +175,17 @@ def xdrop_count_cells_device(ctx, packed_ptr, n_words, read_off_ptr, read_len_pt
                                            ctypes.byref(sc), ctypes.c_void_p(cells_ptr)), ctx)
 
 
+def xdrop_set_tile(ctx, lanes, cells):
+    _check(load().xdrop_set_tile(ctx, int(lanes), int(cells)), ctx)
+
+
+def xdrop_last_spills(ctx, cap=1 << 24) -> np.ndarray:
+    n = ctypes.c_size_t()
+    buf = np.zeros(max(int(cap), 1), np.uint32)
+    _check(load().xdrop_last_spills(ctx, _p(buf), int(cap), ctypes.byref(n)), ctx)
+    return buf[: min(int(n.value), int(cap))]
+
+
 # ---------------------------------------------------------------------------
 # Convenience layer over the C calls (still marshalling only).
 # ---------------------------------------------------------------------------
@@ -222,6 +237,13 @@ class Aligner:
 
     def stats(self):
         return xdrop_get_stats(self.ctx)
+
+    def set_tile(self, lanes, cells):
+        xdrop_set_tile(self.ctx, lanes, cells)
+
+    def tile(self):
+        st = self.stats()
+        return int(st["tile_lanes"]), int(st["tile_cells"])
 
     def stream(self):
         return xdrop_stream(self.ctx)

@@ -106,6 +106,23 @@ def test_other_scorings(X, aligners, orc, mode, scores):
     assert_same(run_host(X, aligners[mode], w), oracle_results(orc, w), f"{mode} {scores}")
 
 
+TILES = [(4, 16), (8, 8), (16, 4), (8, 16), (16, 8), (32, 4)]
+
+
+@pytest.mark.parametrize("tile", TILES, ids=lambda t: f"{t[0]}x{t[1]}")
+def test_every_first_tile(X, orc, tile):
+    """Each first-tier tile (forced, no autotuning) is exact on long,
+    ragged and wide-band inputs."""
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        al.set_tile(*tile)
+        for w in (W.template_pairs(n_pairs=60, seed=21),
+                  W.tiny_pairs(n_pairs=200, seed=22, x=9),
+                  W.template_pairs(n_pairs=16, len_lo=500, len_hi=900, seed=23, x=300)):
+            got = run_host(X, al, w)
+            assert al.tile() == tile
+            assert_same(got, oracle_results(orc, w), f"tile {tile} {w.name}")
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_wide_bands_use_every_tier(X, aligners, orc, mode):
     """Large X widens the live band past the 64-, 128- and 512-slot
