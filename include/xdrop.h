@@ -62,6 +62,7 @@ extern "C" {
 /* xdrop_result.status values (per pair). */
 #define XDROP_STATUS_OK 0
 #define XDROP_STATUS_INVALID 1 /* device submit only: pair failed the limits */
+#define XDROP_STATUS_TOO_LONG 2 /* xdrop_align_static: extension longer than its scratch */
 
 typedef struct xdrop_ctx xdrop_ctx;   /* opaque, owned by the library */
 typedef uint64_t xdrop_ticket;
@@ -178,6 +179,42 @@ int xdrop_count_cells_device(xdrop_ctx *c, const uint32_t *packed,
                              const uint32_t *read_len, uint32_t n_reads,
                              const xdrop_pair *pairs, size_t n_pairs,
                              const xdrop_scoring *s, int64_t *cells);
+
+/* Allocation-free alignment (the paper has no counterpart; this serves
+ * callers that cannot allocate device memory when they align: a process
+ * whose device memory belongs to another allocator, a latency-critical
+ * path that cannot pay for cudaMalloc/cudaFree and their implicit
+ * synchronisation, or work issued while a stream is being captured).
+ *
+ * Same inputs and results as xdrop_submit_device, all in DEVICE memory of
+ * the current device and owned by the caller; the work is enqueued on
+ * `stream` (a cudaStream_t, NULL for the default stream) and the call
+ * returns without waiting: results are in `out` once that stream has
+ * reached this point.  No context is needed and no device memory is
+ * allocated: the scratch is a static 32 MiB array inside the library that
+ * every device using the library holds until the process exits.  The first
+ * call on a device looks the array up (make that first call before any
+ * stream capture that should contain later calls).  All calls on a device
+ * share the array: calls whose work may overlap on the GPU race and must
+ * be ordered (same stream, or events).  Every extension runs on the
+ * unbounded-band tier (one CTA per extension), which is exact for any band
+ * but slower than the batched path.
+ *
+ * max_read_len must bound every read length; it sizes the per-CTA scratch
+ * (3*(max_read_len+1) int32 per extension) and values above 2,796,202
+ * return XDROP_EINVAL.  Pairs that fail the limits get status
+ * XDROP_STATUS_INVALID and zero scores; an extension longer than
+ * max_read_len allows gets XDROP_STATUS_TOO_LONG.  Returns XDROP_OK once
+ * the work is enqueued, XDROP_EINVAL for bad arguments, XDROP_ECUDA if the
+ * launch failed (message from xdrop_static_last_error). */
+int xdrop_align_static(const uint32_t *packed, uint64_t n_words,
+                       const uint64_t *read_off, const uint32_t *read_len,
+                       uint32_t n_reads, const xdrop_pair *pairs, size_t n_pairs,
+                       const xdrop_scoring *s, uint32_t max_read_len,
+                       xdrop_result *out, void *stream);
+
+/* The calling thread's last error message from xdrop_align_static. */
+const char *xdrop_static_last_error(void);
 
 #ifdef __cplusplus
 }

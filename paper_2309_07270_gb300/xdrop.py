@@ -25,6 +25,7 @@ XDROP_MODE_BATCHED = 0
 XDROP_MODE_PLAIN = 1
 XDROP_STATUS_OK = 0
 XDROP_STATUS_INVALID = 1
+XDROP_STATUS_TOO_LONG = 2
 
 PAIR_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("seed_a", "<u4"),
                        ("seed_b", "<u4"), ("seed_len", "<u4")])
@@ -35,7 +36,8 @@ RESULT_DTYPE = np.dtype([("left_score", "<i4"), ("left_begin_a", "<i4"),
 
 EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_free", "xdrop_last_error", "xdrop_stream", "xdrop_get_stats",
-           "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile"]
+           "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
+           "xdrop_align_static", "xdrop_static_last_error"]
 
 
 class XdropError(RuntimeError):
@@ -87,6 +89,11 @@ def load():
                                              ctypes.POINTER(Scoring), vp]
     lib.xdrop_last_spills.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     lib.xdrop_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
+                                       u32, vp, vp]
+    lib.xdrop_align_static.restype = ctypes.c_int
+    lib.xdrop_static_last_error.argtypes = []
+    lib.xdrop_static_last_error.restype = ctypes.c_char_p
     for name in ("xdrop_set_tile", "xdrop_last_spills", "xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
                  "xdrop_get_stats", "xdrop_count_cells_device"):
         getattr(lib, name).restype = ctypes.c_int
@@ -173,6 +180,24 @@ def xdrop_count_cells_device(ctx, packed_ptr, n_words, read_off_ptr, read_len_pt
                                            ctypes.c_void_p(read_len_ptr), int(n_reads),
                                            ctypes.c_void_p(pairs_ptr), int(n_pairs),
                                            ctypes.byref(sc), ctypes.c_void_p(cells_ptr)), ctx)
+
+
+def xdrop_align_static(packed_ptr, n_words, read_off_ptr, read_len_ptr, n_reads, pairs_ptr,
+                       n_pairs, sc: Scoring, max_read_len, out_ptr, stream=0):
+    """Allocation-free alignment: device pointers (ints), enqueued on
+    ``stream`` (a raw cudaStream_t value, 0 for the default stream)."""
+    lib = load()
+    rc = lib.xdrop_align_static(ctypes.c_void_p(packed_ptr), int(n_words),
+                                ctypes.c_void_p(read_off_ptr), ctypes.c_void_p(read_len_ptr),
+                                int(n_reads), ctypes.c_void_p(pairs_ptr), int(n_pairs),
+                                ctypes.byref(sc), int(max_read_len), ctypes.c_void_p(out_ptr),
+                                ctypes.c_void_p(stream))
+    if rc != XDROP_OK:
+        raise XdropError(rc, lib.xdrop_static_last_error().decode())
+
+
+def xdrop_static_last_error() -> str:
+    return load().xdrop_static_last_error().decode()
 
 
 def xdrop_set_tile(ctx, lanes, cells):
