@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--pairs", type=int, default=0,
                     help="use only the first N pairs (small cases for profiling)")
     ap.add_argument("--tile", default="", help="force the first tile, e.g. 8x8 (no autotune)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving sweep only: 4 launch policies x load 0.5/0.75/1.0")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -60,6 +64,17 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(value, device):
+    """Maximum of a per-rank float over all ranks (timing only; no data)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload(x, pairs=0):
@@ -225,6 +240,26 @@ def traffic_from_profile(kernel_tag):
     return None
 
 
+def run_serving(w, sc, capacity_pairs_s, policies, rhos, seconds, device, tile=None):
+    """25 producers with Poisson arrivals of U[1k, 20k]-pair batches drawn
+    from the workload's pairs (seeds 100+p), at rho x the measured batched
+    capacity.  Returns one summary per (rho, policy)."""
+    from paper_2309_07270_gb300 import serving
+    from paper_2309_07270_gb300 import workloads as W
+    runs = []
+    for rho in rhos:
+        sched = W.serving_schedule(w.n_pairs, n_producers=25,
+                                   rate_pairs_per_s=rho * capacity_pairs_s,
+                                   duration_s=seconds, seed_base=100)
+        for pol in policies:
+            r = serving.run_policy(pol, w, sched, sc, device=device, tile=tile, rho=rho,
+                                   offered=rho * capacity_pairs_s)
+            s = r.summary()
+            s["seconds"] = seconds
+            runs.append(s)
+    return runs
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -294,12 +329,7 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
 
-    mean_ms = statistics.mean(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([mean_ms], device=dev_name)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        mean_ms = float(tt.item())
+    mean_ms = max_over_ranks(statistics.mean(step_ms), dev_name)
     value = ws * cells / (mean_ms * 1e-3) / 1e9
     pairs_s = ws * w.n_pairs / (mean_ms * 1e-3)
 
@@ -338,12 +368,7 @@ def run_ours(args):
             if k >= args.warmup:
                 ets.append(dt)
         assert (hout.view(np.int32) == res.view(np.int32)).all()
-        em = statistics.mean(ets)
-        if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([em], device=dev_name)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            em = float(tt.item())
+        em = max_over_ranks(statistics.mean(ets), dev_name)
         e2e = {"value": ws * cells / em / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(hp.nbytes + ho.nbytes + hl.nbytes + hpairs.nbytes),
                "d2h_bytes_per_step": int(hout.nbytes), "pairs_per_s": ws * w.n_pairs / em,
@@ -366,6 +391,11 @@ def run_ours(args):
             "ops_per_cell": INT_OPS_PER_CELL, "cells_in_kernel": cells_tier0,
             "step_frac": INT_OPS_PER_CELL * cells / (mean_ms * 1e-3) / 1e12 / peak}
 
+    serving_runs = None
+    if not args.no_serve:
+        serving_runs = run_serving(w, sc, pairs_s / ws, ["device-loop"], [0.75],
+                                   args.serve_seconds, local)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, args.cpu_seconds)
@@ -385,6 +415,7 @@ def run_ours(args):
                 "pairs_per_s": pairs_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "plain": plain,
                 "batched_over_plain": (value / plain["value"]) if plain else None,
+                "serving": serving_runs[0] if serving_runs else None,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     batched.close()
@@ -394,10 +425,41 @@ def run_ours(args):
     return 0
 
 
+def run_serve_sweep(args):
+    """Serving sweep: capacity from a short batched measurement, then every
+    launch policy at three loads.  Prints one JSON line."""
+    import torch
+
+    from paper_2309_07270_gb300 import build as B
+    from paper_2309_07270_gb300 import xdrop as X
+    B.build()
+    w = workload(args.x, args.pairs)
+    sc = X.scoring(w.match, w.mismatch, w.gap, w.x)
+    dev = X.DeviceInputs.from_workload(w)
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        times = []
+        for k in range(6):
+            al.align_device(dev, sc)
+            if k >= 3:
+                times.append(al.stats()["kernel_ms"])
+        ms = min(times)
+    del dev
+    torch.cuda.empty_cache()
+    capacity = w.n_pairs / (ms * 1e-3)
+    runs = run_serving(w, sc, capacity, ["device-loop", "per-producer-streams", "ring-subbatch",
+                                         "ring-batch"], [0.5, 0.75, 1.0], args.serve_seconds, 0)
+    print(json.dumps({"metric": METRIC, "mode": "serving sweep", "capacity_pairs_per_s": capacity,
+                      "producers": 25, "batch_pairs": [1000, 20000],
+                      "config": workload_config(w), "runs": runs}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve_sweep(args)
     return run_ours(args)
 
 

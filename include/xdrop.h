@@ -58,6 +58,8 @@ extern "C" {
 /* xdrop_init flags. */
 #define XDROP_MODE_BATCHED 0u /* default: binned persistent launch in a graph */
 #define XDROP_MODE_PLAIN 1u   /* one launch per 10,000-pair sub-batch         */
+#define XDROP_MODE_SERVE 2u   /* batched, plus continuous batching of
+                                 xdrop_submit_pairs requests (serving)       */
 
 /* xdrop_result.status values (per pair). */
 #define XDROP_STATUS_OK 0
@@ -103,8 +105,25 @@ typedef struct {
     uint32_t tile_cells;     /* first band tier: cells per lane           */
 } xdrop_stats;
 
+typedef struct {
+    uint64_t requests_done;   /* serving requests completed                  */
+    uint64_t wide_passes;     /* requests whose widest-band extensions ran
+                                 the 512-slot / unbounded tiers beside the
+                                 serving kernel                              */
+    uint64_t relaunches;      /* serving kernel launches                     */
+    uint64_t max_in_flight;   /* most requests admitted at once              */
+    uint64_t admission_waits; /* admissions deferred for lack of memory      */
+    uint64_t published;       /* extensions published to the task ring       */
+    uint64_t consumed;        /* extensions taken from it                    */
+    uint64_t spill_reserved;  /* extensions handed to the second tier        */
+    uint64_t spill_taken;     /* of those, taken by second-tier groups       */
+    uint64_t ring_warps;      /* first-tier warps of the running kernel      */
+} xdrop_serve_stats;
+
 /* Create a context on CUDA device `device`.  device_mem_budget bounds the
- * device memory the context holds at once (0: no bound).  flags:
+ * device memory the context holds at once (0: no bound); in serving mode it
+ * bounds the buffers of the requests in flight (memory admission; 0: 1 GiB)
+ * and the resident reads and scratch are not counted.  flags:
  * XDROP_MODE_*.  On success *out owns a stream, events and buffers; free
  * it with xdrop_free.  Returns XDROP_OK, XDROP_EINVAL or XDROP_ECUDA. */
 int xdrop_init(xdrop_ctx **out, int device, size_t device_mem_budget,
@@ -134,6 +153,30 @@ int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
                         uint32_t n_reads, const xdrop_pair *pairs,
                         size_t n_pairs, const xdrop_scoring *s,
                         xdrop_result *out, xdrop_ticket *t);
+
+/* Make a read set resident on the device for xdrop_submit_pairs (host
+ * memory, same layout and limits as xdrop_submit; copied before return).
+ * Replaces the previous read set; in serving mode it first waits for the
+ * requests in flight.  Returns XDROP_OK, XDROP_EINVAL or XDROP_ECUDA. */
+int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
+                     const uint32_t *read_len, uint32_t n_reads);
+
+/* Align n_pairs pairs (HOST memory, copied before return) against the
+ * resident read set.  Results go to `out` (host memory, valid until the
+ * ticket's sync returns XDROP_OK).  Pairs are validated first
+ * (XDROP_EINVAL, nothing queued).
+ *
+ * Serving mode (XDROP_MODE_SERVE): thread-safe continuous batching.  The
+ * request is queued, admitted once a slot is free and its device buffers
+ * fit the context's memory budget (XDROP_ENOMEM if they never can), and
+ * its extensions are appended to the work of a persistent kernel that is
+ * already running other requests; results are identical to a request run
+ * alone.  Other modes: an ordinary submit over the resident reads. */
+int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
+                       const xdrop_scoring *s, xdrop_result *out, xdrop_ticket *t);
+
+/* Counters of the serving loop (all zero outside serving mode). */
+int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st);
 
 /* Wait for a ticket.  timeout_ns < 0 waits without bound; otherwise the
  * call returns XDROP_ETIMEDOUT after about timeout_ns and the ticket stays

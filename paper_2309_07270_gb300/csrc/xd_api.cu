@@ -27,6 +27,7 @@
 
 #include "../../include/xdrop.h"
 #include "xd_launch.h"
+#include "xd_serve.h"
 
 using namespace xd;
 
@@ -130,7 +131,18 @@ struct xdrop_ctx {
     uint64_t graph_version = ~0ull;
 
     xdrop_stats last = {};
+
+    // resident reads (xdrop_load_reads) and the serving loop
+    DevBuf r_packed, r_off, r_len;
+    std::vector<uint64_t> h_off;
+    std::vector<uint32_t> h_len;
+    uint64_t r_words = 0;
+    uint32_t r_n = 0, r_maxlen = 0;
+    bool have_reads = false;
+    xd::Server *srv = nullptr;
 };
+
+constexpr uint64_t kServeTicket = 1ull << 63;
 
 namespace {
 
@@ -138,7 +150,8 @@ int dev_alloc(xdrop_ctx *c, DevBuf &b, size_t bytes)
 {
     if (b.cap >= bytes) return XDROP_OK;
     size_t nb = std::max(bytes, b.cap + b.cap / 2);
-    if (c->budget && c->used - b.cap + nb > c->budget) {
+    // In serving mode the budget bounds the requests in flight instead.
+    if (c->budget && c->mode != XDROP_MODE_SERVE && c->used - b.cap + nb > c->budget) {
         nb = bytes;
         if (c->used - b.cap + nb > c->budget)
             return fail(c->tickets.empty() ? XDROP_ENOMEM : XDROP_EBUSY,
@@ -415,7 +428,7 @@ int xdrop_init(xdrop_ctx **out, int device, size_t budget, uint32_t flags)
 {
     if (!out) return fail(XDROP_EINVAL, "out is NULL");
     *out = nullptr;
-    if (flags & ~1u) return fail(XDROP_EINVAL, "unknown flags 0x%x", flags);
+    if (flags > XDROP_MODE_SERVE) return fail(XDROP_EINVAL, "unknown flags 0x%x", flags);
     int n = 0;
     CK(cudaGetDeviceCount(&n));
     if (device < 0 || device >= n) return fail(XDROP_EINVAL, "no CUDA device %d", device);
@@ -423,7 +436,7 @@ int xdrop_init(xdrop_ctx **out, int device, size_t budget, uint32_t flags)
     xdrop_ctx *c = new xdrop_ctx();
     c->device = device;
     c->budget = budget;
-    c->mode = flags & 1u;
+    c->mode = flags;
     cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_job, sizeof(Job));
@@ -509,7 +522,7 @@ int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
         free_ticket(c, tk);
         return fail(XDROP_ECUDA, "input copy: %s", cudaGetErrorString(e));
     }
-    Job job;
+    Job job{};
     job.packed = (const uint32_t *)(d + o_packed);
     job.n_words = (int64_t)std::max<uint64_t>(n_words, 1);
     job.read_off = (const uint64_t *)(d + o_off);
@@ -559,7 +572,7 @@ int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
     }
     Ticket *tk = nullptr;
     if ((rc = new_ticket(c, n_pairs, true, &tk))) return rc;
-    Job job;
+    Job job{};
     job.packed = packed;
     job.n_words = (int64_t)n_words;
     job.read_off = read_off;
@@ -584,6 +597,12 @@ int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
 int xdrop_sync(xdrop_ctx *c, xdrop_ticket t, int64_t timeout_ns)
 {
     if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    if (t & kServeTicket) {
+        if (!c->srv) return fail(XDROP_EINVAL, "unknown ticket %llu", (unsigned long long)t);
+        std::string err;
+        const int rc = xd::server_sync(c->srv, t & ~kServeTicket, timeout_ns, err);
+        return rc ? fail(rc, "%s", err.c_str()) : XDROP_OK;
+    }
     Ticket *tk = nullptr;
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -639,6 +658,10 @@ void xdrop_free(xdrop_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    if (c->srv) xd::server_destroy(c->srv);
+    cudaFree(c->r_packed.p);
+    cudaFree(c->r_off.p);
+    cudaFree(c->r_len.p);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &kv : c->tickets) free_ticket(c, kv.second);
     c->tickets.clear();
@@ -667,6 +690,160 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st)
     if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
     *st = c->last;
+    return XDROP_OK;
+}
+
+int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
+                     const uint32_t *read_len, uint32_t n_reads)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    if (n_reads && (!packed || !read_off || !read_len)) return fail(XDROP_EINVAL, "NULL input array");
+    uint64_t n_words = 0;
+    uint32_t maxlen = 0;
+    for (uint32_t r = 0; r < n_reads; ++r) {
+        if (read_off[r] & 15) return fail(XDROP_EINVAL, "read %u offset not a multiple of 16", r);
+        if ((int64_t)read_len[r] >= LEN_LIMIT) return fail(XDROP_EINVAL, "read %u too long", r);
+        n_words = std::max<uint64_t>(n_words, (read_off[r] + read_len[r] + 15) / 16);
+        maxlen = std::max(maxlen, read_len[r]);
+    }
+    if (n_words * 16 >= ((uint64_t)1 << 32)) return fail(XDROP_EINVAL, "packed buffer too large");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    if (c->srv) {  // waits for the serving requests in flight
+        xd::server_destroy(c->srv);
+        c->srv = nullptr;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    int rc;
+    const uint64_t nw = std::max<uint64_t>(n_words, 1);
+    if ((rc = dev_alloc(c, c->r_packed, nw * 4))) return rc;
+    if ((rc = dev_alloc(c, c->r_off, std::max<size_t>(n_reads, 1) * 8))) return rc;
+    if ((rc = dev_alloc(c, c->r_len, std::max<size_t>(n_reads, 1) * 4))) return rc;
+    if (n_words) CK(cudaMemcpy(c->r_packed.p, packed, n_words * 4, cudaMemcpyHostToDevice));
+    if (n_reads) {
+        CK(cudaMemcpy(c->r_off.p, read_off, (size_t)n_reads * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->r_len.p, read_len, (size_t)n_reads * 4, cudaMemcpyHostToDevice));
+    }
+    c->h_off.assign(read_off, read_off + n_reads);
+    c->h_len.assign(read_len, read_len + n_reads);
+    c->r_words = nw;
+    c->r_n = n_reads;
+    c->r_maxlen = maxlen;
+    c->have_reads = true;
+    if ((rc = ensure_scratch(c, 0, maxlen))) return rc;
+    if (c->mode == XDROP_MODE_SERVE) {
+        xd::ResidentReads rr;
+        rr.packed = (const uint32_t *)c->r_packed.p;
+        rr.n_words = (int64_t)nw;
+        rr.read_off = (const uint64_t *)c->r_off.p;
+        rr.read_len = (const uint32_t *)c->r_len.p;
+        rr.n_reads = n_reads;
+        std::string err;
+        const Tile t = c->forced.lanes ? c->forced : Tile{4, 16};
+        c->srv = xd::server_create(c->device, c->sm_count, c->budget, t, rr, c->h_len.data(),
+                                   (int32_t *)c->wide.p, c->wide_per_cta, c->wide_grid, err);
+        if (!c->srv) return fail(XDROP_ECUDA, "%s", err.c_str());
+    }
+    return XDROP_OK;
+}
+
+int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
+                       const xdrop_scoring *s, xdrop_result *out, xdrop_ticket *t)
+{
+    if (!c || !t) return fail(XDROP_EINVAL, "context or ticket pointer is NULL");
+    int rc = validate_scoring(s);
+    if (rc) return rc;
+    if (n_pairs && (!pairs || !out)) return fail(XDROP_EINVAL, "NULL input array");
+    if (2 * (uint64_t)n_pairs >= ((uint64_t)1 << 32))
+        return fail(XDROP_EINVAL, "too many pairs in one submit");
+    const Scoring sc{s->match, s->mismatch, s->gap, s->x};
+    xd::Server *srv = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->have_reads) return fail(XDROP_EINVAL, "no resident reads (xdrop_load_reads)");
+        for (size_t p = 0; p < n_pairs; ++p) {
+            const Pair &pr = *(const Pair *)&pairs[p];
+            if (!pair_ok(pr, c->r_n, c->h_len.data(), c->h_off.data(), (int64_t)c->r_words, sc))
+                return fail(XDROP_EINVAL, "pair %zu is invalid (read id, seed or length limit)", p);
+        }
+        srv = c->srv;
+    }
+    if (srv) {
+        std::string err;
+        uint64_t id = 0;
+        rc = xd::server_submit(srv, pairs, n_pairs, sc, out, &id, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+        *t = id | kServeTicket;
+        return XDROP_OK;
+    }
+    // not serving: an ordinary ticket over the resident reads
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    Ticket *tk = nullptr;
+    if ((rc = new_ticket(c, n_pairs, false, &tk))) return rc;
+    tk->out = out;
+    const size_t o_out = align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_pair));
+    const size_t bytes = o_out + align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_result));
+    if (c->budget && c->used + bytes > c->budget) {
+        free_ticket(c, tk);
+        return fail(c->tickets.empty() ? XDROP_ENOMEM : XDROP_EBUSY,
+                    "device memory budget exceeded (%zu bytes needed)", bytes);
+    }
+    cudaError_t e = cudaMalloc(&tk->d_mem, bytes);
+    if (e != cudaSuccess) {
+        free_ticket(c, tk);
+        return fail(XDROP_ECUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    tk->d_bytes = bytes;
+    c->used += bytes;
+    char *d = (char *)tk->d_mem;
+    if (n_pairs) e = cudaMemcpyAsync(d, pairs, n_pairs * sizeof(xdrop_pair), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && n_pairs)
+        e = cudaMemsetAsync(d + o_out, 0, n_pairs * sizeof(xdrop_result), c->stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);
+        free_ticket(c, tk);
+        return fail(XDROP_ECUDA, "input copy: %s", cudaGetErrorString(e));
+    }
+    Job job{};
+    job.packed = (const uint32_t *)c->r_packed.p;
+    job.n_words = (int64_t)c->r_words;
+    job.read_off = (const uint64_t *)c->r_off.p;
+    job.read_len = (const uint32_t *)c->r_len.p;
+    job.n_reads = c->r_n;
+    job.pairs = (const Pair *)d;
+    job.n_pairs = n_pairs;
+    job.sc = sc;
+    job.out = (int32_t *)(d + o_out);
+    if ((rc = launch_ticket(c, tk, job, c->r_maxlen))) {
+        cudaStreamSynchronize(c->stream);
+        free_ticket(c, tk);
+        return rc;
+    }
+    tk->id = c->next_id++;
+    c->tickets[tk->id] = tk;
+    *t = tk->id;
+    return XDROP_OK;
+}
+
+int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st)
+{
+    if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");
+    memset(st, 0, sizeof(*st));
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->srv) {
+        const xd::ServerStats s = xd::server_stats(c->srv);
+        st->requests_done = s.requests_done;
+        st->wide_passes = s.wide_passes;
+        st->relaunches = s.relaunches;
+        st->max_in_flight = s.max_in_flight;
+        st->admission_waits = s.admission_waits;
+        st->published = s.published;
+        st->consumed = s.consumed;
+        st->spill_reserved = s.spill_reserved;
+        st->spill_taken = s.spill_taken;
+        st->ring_warps = s.ring_warps;
+    }
     return XDROP_OK;
 }
 
@@ -720,7 +897,7 @@ int xdrop_count_cells_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_wo
     CK(cudaMemcpyAsync(&maxlen, c->d_ctrs + C_MAXLEN, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if ((rc = ensure_scratch(c, 2 * n_pairs, maxlen))) return rc;
-    Job job;
+    Job job{};
     job.packed = packed;
     job.n_words = (int64_t)n_words;
     job.read_off = read_off;

@@ -481,26 +481,131 @@ __device__ __forceinline__ int32_t dp_step_key(int32_t (&V)[C], const int32_t (&
     return lkey;
 }
 
-template <int L, int C>
-__global__ void __launch_bounds__(256)
-lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_ptr,
-                uint32_t *counter, Spill spill)
+// Result of one finished task (written by the group leader).
+__device__ __forceinline__ void store_result(const Job &J, uint32_t task, int32_t T, int32_t bi,
+                                             int32_t bj)
+{
+    const Pair p = J.pairs[task >> 1];
+    int32_t *o = J.out + (size_t)(task >> 1) * 7;
+    if (task & 1u) {
+        o[3] = T;
+        o[4] = (int32_t)(p.seed_a + p.seed_len) + bi;
+        o[5] = (int32_t)(p.seed_b + p.seed_len) + bj;
+    } else {
+        o[0] = T;
+        o[1] = (int32_t)p.seed_a - bi;
+        o[2] = (int32_t)p.seed_b - bj;
+    }
+}
+
+// Serving rewrites a slot's Job and pair buffer between requests while the
+// persistent kernel runs, so those reads must not be served from an SM's
+// L1: load them at L2 (ld.global.cg).
+__device__ __forceinline__ Job ldcg_job(const Job *gj)
+{
+    static_assert(sizeof(Job) % 8 == 0, "Job layout");
+    Job J;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(gj);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&J);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(Job) / 8); ++k) dst[k] = __ldcg(src + k);
+    return J;
+}
+
+__device__ __forceinline__ Pair ldcg_pair(const Pair *p)
+{
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(p);
+    return Pair{__ldcg(w), __ldcg(w + 1), __ldcg(w + 2), __ldcg(w + 3), __ldcg(w + 4)};
+}
+
+// decode() / store_result() for a serving Job (L2 loads of the request's data).
+__device__ __forceinline__ Ext decode_cg(const Job &J, uint32_t task)
+{
+    Job K = J;
+    Pair p = ldcg_pair(&J.pairs[task >> 1]);
+    // decode() reads the pair through K.pairs; hand it a one-record view.
+    K.pairs = &p;
+    Ext e = decode(K, (task & 1u));
+    e.pair = task >> 1;
+    return e;
+}
+
+__device__ __forceinline__ void store_result_cg(const Job &J, uint32_t task, int32_t T,
+                                                int32_t bi, int32_t bj)
+{
+    const Pair p = ldcg_pair(&J.pairs[task >> 1]);
+    int32_t *o = J.out + (size_t)(task >> 1) * 7;
+    if (task & 1u) {
+        o[3] = T;
+        o[4] = (int32_t)(p.seed_a + p.seed_len) + bi;
+        o[5] = (int32_t)(p.seed_b + p.seed_len) + bj;
+    } else {
+        o[0] = T;
+        o[1] = (int32_t)p.seed_a - bi;
+        o[2] = (int32_t)p.seed_b - bj;
+    }
+}
+
+// Task source of the batched form: positions of a longest-first order
+// array pulled from a global counter; overflowing tasks go to a spill list.
+struct BatchSrc {
+    const Job *jp;
+    const uint32_t *order;
+    uint32_t n_tasks;
+    uint32_t *counter;
+    Spill spill;
+
+    // Warp-level fetch, executed by every lane: the leaders of the groups
+    // that need a task are the set bits of needm.  Returns, for this lane's
+    // group, 1 (task), 0 (nothing yet) or -1 (no more tasks).
+    __device__ __forceinline__ int fetch_warp(unsigned needm, int lane, int gbase, unsigned gm,
+                                              bool need, uint32_t &task, const Job *&gj)
+    {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(counter, (uint32_t)__popc(needm));
+        base = __shfl_sync(FULL, base, 0);
+        if (!need) return 0;
+        const uint32_t q = base + (uint32_t)__popc(needm & ((1u << gbase) - 1u));
+        if (q >= n_tasks) return -1;
+        task = order ? order[q] : q;
+        gj = jp;
+        return 1;
+    }
+    __device__ __forceinline__ void idle() {}
+    __device__ __forceinline__ bool aborted() const { return false; }
+    __device__ __forceinline__ Ext open(const Job *gj, uint32_t task, Scoring &sc)
+    {
+        sc = gj->sc;
+        return decode(*gj, task);
+    }
+    // called by the group leader only
+    __device__ __forceinline__ void retire(const Job *gj, uint32_t task, bool overflow, int32_t T,
+                                           int32_t bi, int32_t bj)
+    {
+        if (overflow) {
+            const uint32_t q = atomicAdd(spill.count, 1u);
+            spill.list[q] = task;
+        } else {
+            store_result(*gj, task, T, bi, bj);
+        }
+    }
+};
+
+template <int L, int C, class Src>
+__device__ __forceinline__ void lockstep_loop(Src &src, const uint32_t *pk, int64_t nw)
 {
     static_assert(C <= 16 && 32 % L == 0, "tile shape");
     constexpr int W = L * C;
-    const Job J = *jp;
-    const Scoring sc = J.sc;
-    const uint32_t *pk = J.packed;
-    const int64_t nw = J.n_words;
     const int lane = threadIdx.x & 31;
     const int glane = lane % L;
     const int gbase = lane - glane;
     const unsigned gm = group_mask<L>(gbase);
-    const uint32_t n_tasks = *n_tasks_ptr;
 
     // Per-group task state (uniform within a group).
     bool active = false, exhausted = false;
     uint32_t task = 0;
+    const Job *gj = nullptr;
+    Scoring sc{1, -1, -1, 0};
     int64_t sa0 = 0, sb0 = 0;  // stream anchors of a and b
     int dir = 1;
     int32_t m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
@@ -513,24 +618,7 @@ lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_pt
 
     // End of a task: result (or hand-off to the next tier) by the leader.
     auto retire = [&](bool overflow) {
-        if (glane == 0) {
-            if (overflow) {
-                const uint32_t q = atomicAdd(spill.count, 1u);
-                spill.list[q] = task;
-            } else {
-                const Pair p = J.pairs[task >> 1];
-                int32_t *o = J.out + (size_t)(task >> 1) * 7;
-                if (task & 1u) {
-                    o[3] = T;
-                    o[4] = (int32_t)(p.seed_a + p.seed_len) + bi;
-                    o[5] = (int32_t)(p.seed_b + p.seed_len) + bj;
-                } else {
-                    o[0] = T;
-                    o[1] = (int32_t)p.seed_a - bi;
-                    o[2] = (int32_t)p.seed_b - bj;
-                }
-            }
-        }
+        if (glane == 0) src.retire(gj, task, overflow, T, bi, bj);
         active = false;
     };
 
@@ -541,10 +629,10 @@ lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_pt
         const int32_t mkey = __reduce_max_sync(gm, lkey);
         const int32_t M = mkey >> 4;
         const unsigned hits = __ballot_sync(FULL, (lkey >> 4) == M) & gm;
-        const int src = __ffs(hits) - 1;
-        const int32_t skey = __shfl_sync(FULL, lkey, src);
+        const int src_lane = __ffs(hits) - 1;
+        const int32_t skey = __shfl_sync(FULL, lkey, src_lane);
         if (active && M > T) {
-            bi = (i0 - glane * C) + (src - gbase) * C + (15 - (skey & 15));
+            bi = (i0 - glane * C) + (src_lane - gbase) * C + (15 - (skey & 15));
             bj = d - bi;
             T = M;
         }
@@ -598,19 +686,20 @@ lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_pt
         if (fin) retire(ovf);
     };
 
+    unsigned turn = 0;
     for (;;) {
+        // A serving kernel can be told to leave at once (teardown).
+        if ((++turn & 255u) == 0 && __any_sync(FULL, src.aborted())) break;
         // ---------------- task switches (top of an odd diagonal) ----------------
         const bool need = !active && !exhausted;
-        if (__any_sync(FULL, need)) {
+        const unsigned needm = __ballot_sync(FULL, need && glane == 0);
+        if (needm) {
+            const int r = src.fetch_warp(needm, lane, gbase, gm, need, task, gj);
             if (need) {
-                uint32_t q = 0;
-                if (glane == 0) q = atomicAdd(counter, 1u);
-                q = __shfl_sync(gm, q, gbase);
-                if (q >= n_tasks) {
+                if (r < 0) {
                     exhausted = true;
-                } else {
-                    task = order ? order[q] : q;
-                    const Ext e = decode(J, task);
+                } else if (r > 0) {
+                    const Ext e = src.open(gj, task, sc);
                     if (e.ok) {
                         sa0 = e.A.s0;
                         sb0 = e.B.s0;
@@ -639,7 +728,10 @@ lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_pt
             }
         }
         if (__all_sync(FULL, exhausted && !active)) break;
-        if (!__any_sync(FULL, active)) continue;
+        if (!__any_sync(FULL, active)) {
+            src.idle();
+            continue;
+        }
 
         // ---------------- odd diagonal: a-window advances ----------------
         ++d;
@@ -688,6 +780,328 @@ lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_pt
             finish(E, lkey, false);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a persistent kernel fed by a device ring of tasks that the host
+// keeps appending to while the kernel runs (continuous batching).  Ring
+// entry = slot << 24 | task; slot names the request's device Job.
+//
+// Most warps run the first-tier tile on ring tasks.  A task whose band
+// outgrows that tile goes to a device spill queue, which one warp in
+// sixteen serves with the next wider tile, so overflow never stops the
+// loop.  A task too wide for the second tier is listed in its request
+// (Job::spill_list, counted in ctr[1]) for the host's unbounded pass.
+// Every wait is bounded: ring warps leave after an idle limit (or on stop /
+// yield), spill warps once every ring warp has left and their queue is
+// empty; a queue entry that never appears sets the error word.
+// ---------------------------------------------------------------------------
+constexpr int kSpillWarpEvery = 16;
+constexpr uint32_t kSpillQueueMask = (1u << 16) - 1;
+constexpr int kEntrySpinLimit = 1 << 20;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct ServeArgs {
+    ServeCtl *ctl;
+    const uint32_t *ring;
+    uint32_t ring_mask;
+    uint32_t *spq;             // spill queue, entry + 1 (0 = empty)
+    const Job *slot_jobs;
+    uint32_t *done;            // mapped host: per slot tag and wide count; [2*64] error word
+    uint32_t n_slots;
+};
+
+// Count a finished task; the last one of a request publishes it.
+__device__ __forceinline__ void serve_count(const ServeArgs &a, const Job *gj, const Job &J)
+{
+    __threadfence();
+    const uint32_t f = atomicAdd(&J.ctr[0], 1u) + 1u;
+    if ((uint64_t)f == 2 * J.n_pairs) {
+        const size_t sl = (size_t)(gj - a.slot_jobs);
+        volatile uint32_t *d = a.done;
+        d[2 * sl + 1] = *(volatile const uint32_t *)&J.ctr[1];
+        __threadfence_system();
+        d[2 * sl] = J.tag;
+    }
+}
+
+// A task the second tier cannot hold: listed for the host's unbounded pass.
+__device__ __forceinline__ void serve_list_wide(const ServeArgs &a, const Job *gj, const Job &J,
+                                                uint32_t task)
+{
+    const uint32_t k = atomicAdd(&J.ctr[1], 1u);
+    J.spill_list[k] = task;
+    serve_count(a, gj, J);
+}
+
+constexpr unsigned long long kSpillBacklog = 64;  // ring warps switch tiers above this
+
+struct RingSrc {
+    ServeArgs a;
+    unsigned long long idle_since;
+    int backoff;   // loop turns before the next poll (leader)
+    int level;     // backoff doubling level (leader)
+    bool leaving;  // stop, yield or the idle bound (not a switch to the second tier)
+
+    // Warp-level fetch (see BatchSrc): one poll and one CAS for all the
+    // warp's waiting groups; idle warps back off exponentially.
+    __device__ __forceinline__ int fetch_warp(unsigned needm, int lane, int gbase, unsigned gm,
+                                              bool need, uint32_t &task, const Job *&gj)
+    {
+        int status = 0;  // 1 granted k entries, 0 none, -1 leave, -2 help the second tier
+        int k = 0;
+        unsigned long long base = 0;
+        if (lane == 0) {
+            if (backoff > 0) {
+                --backoff;
+            } else {
+                volatile ServeCtl *v = a.ctl;
+                if (v->yield) {
+                    status = -1;
+                } else if (*(volatile unsigned long long *)&a.ctl->spill_tail -
+                               *(volatile unsigned long long *)&a.ctl->spill_head >
+                           kSpillBacklog) {
+                    status = -2;
+                } else {
+                    const unsigned long long pub = v->published;
+                    unsigned long long cons = *(volatile unsigned long long *)&a.ctl->consumed;
+                    const unsigned long long want = (unsigned long long)__popc(needm);
+                    for (int tries = 0; tries < 4 && cons < pub; ++tries) {
+                        const unsigned long long kk = (pub - cons < want) ? pub - cons : want;
+                        const unsigned long long got = atomicCAS(&a.ctl->consumed, cons, cons + kk);
+                        if (got == cons) {
+                            base = cons;
+                            k = (int)kk;
+                            status = 1;
+                            break;
+                        }
+                        cons = got;
+                    }
+                    if (status == 1) {
+                        idle_since = 0;
+                        level = 0;
+                    } else {
+                        const unsigned long long now = globaltimer_ns();
+                        if (idle_since == 0) idle_since = now;
+                        if (v->stop || now - idle_since > v->idle_ns) status = -1;
+                        backoff = 1 << level;
+                        if (level < 6) ++level;
+                    }
+                }
+            }
+        }
+        // every lane takes part in the broadcasts before any lane returns
+        status = __shfl_sync(FULL, status, 0);
+        k = __shfl_sync(FULL, k, 0);
+        base = __shfl_sync(FULL, base, 0);
+        if (status == -1) leaving = true;
+        if (!need) return 0;
+        if (status < 0) return -1;
+        if (status == 0) return 0;
+        const int rank = __popc(needm & ((1u << gbase) - 1u));
+        if (rank >= k) return 0;
+        const uint32_t entry = *(volatile const uint32_t *)&a.ring[(base + rank) & a.ring_mask];
+        task = entry & 0xffffffu;
+        gj = &a.slot_jobs[entry >> 24];
+        return 1;
+    }
+    __device__ __forceinline__ void idle() { __nanosleep(2000); }
+    __device__ __forceinline__ bool aborted() const
+    {
+        return *(volatile const unsigned int *)&a.ctl->abort != 0u;
+    }
+    __device__ __forceinline__ Ext open(const Job *gj, uint32_t task, Scoring &sc)
+    {
+        const Job J = ldcg_job(gj);
+        sc = J.sc;
+        return decode_cg(J, task);
+    }
+    __device__ __forceinline__ void retire(const Job *gj, uint32_t task, bool overflow, int32_t T,
+                                           int32_t bi, int32_t bj)
+    {
+        const Job J = ldcg_job(gj);
+        if (!overflow) {
+            store_result_cg(J, task, T, bi, bj);
+            serve_count(a, gj, J);
+            return;
+        }
+        // Hand the task to the second tier (not counted yet).  Reserve a
+        // queue position only while the queue has room; the slot's previous
+        // occupant (one lap earlier) has been taken, and its taker clears
+        // the slot right after reading it.
+        volatile ServeCtl *v = a.ctl;
+        unsigned long long t = v->spill_tail;
+        for (int tries = 0; tries < 8; ++tries) {
+            if (t - v->spill_head > kSpillQueueMask) break;  // full
+            const unsigned long long got = atomicCAS(&a.ctl->spill_tail, t, t + 1);
+            if (got == t) {
+                volatile uint32_t *slot = (volatile uint32_t *)&a.spq[t & kSpillQueueMask];
+                bool free_slot = false;
+                for (int spin = 0; spin < kEntrySpinLimit; ++spin) {
+                    if (*slot == 0u) { free_slot = true; break; }
+                    __nanosleep(64);
+                }
+                if (!free_slot) {
+                    volatile uint32_t *d = a.done;
+                    d[2 * a.n_slots] = 1u;  // error word: the slot never drained
+                    __threadfence_system();
+                }
+                *slot = (((uint32_t)(gj - a.slot_jobs) << 24) | task) + 1u;
+                return;
+            }
+            t = got;
+        }
+        serve_list_wide(a, gj, J, task);  // queue full or contended: the host's pass
+    }
+};
+
+struct SpillSrc {
+    ServeArgs a;
+    int backoff;
+    int level;
+    bool dynamic;  // a ring warp helping out: leave as soon as the queue is empty
+    bool failed;
+
+    __device__ __forceinline__ int fetch_warp(unsigned needm, int lane, int gbase, unsigned gm,
+                                              bool need, uint32_t &task, const Job *&gj)
+    {
+        int status = 0;  // 1 granted k positions, 0 none, -1 leave
+        int k = 0;
+        unsigned long long base = 0;
+        if (lane == 0) {
+            if (backoff > 0) {
+                --backoff;
+            } else {
+                volatile ServeCtl *v = a.ctl;
+                const unsigned long long tail = *(volatile unsigned long long *)&a.ctl->spill_tail;
+                unsigned long long head = *(volatile unsigned long long *)&a.ctl->spill_head;
+                const unsigned long long want = (unsigned long long)__popc(needm);
+                for (int tries = 0; tries < 4 && head < tail; ++tries) {
+                    const unsigned long long kk = (tail - head < want) ? tail - head : want;
+                    const unsigned long long got = atomicCAS(&a.ctl->spill_head, head, head + kk);
+                    if (got == head) {
+                        base = head;
+                        k = (int)kk;
+                        status = 1;
+                        break;
+                    }
+                    head = got;
+                }
+                if (status == 1) {
+                    level = 0;
+                } else if (head >= tail && (dynamic || v->ring_alive == 0)) {
+                    status = -1;
+                } else if (!dynamic) {
+                    backoff = 1 << level;
+                    if (level < 6) ++level;
+                }
+            }
+        }
+        // every lane takes part in the broadcasts before any lane returns
+        status = __shfl_sync(FULL, status, 0);
+        k = __shfl_sync(FULL, k, 0);
+        base = __shfl_sync(FULL, base, 0);
+        if (!need) return 0;
+        if (status < 0) return -1;
+        if (status == 0) return 0;
+        const int rank = __popc(needm & ((1u << gbase) - 1u));
+        if (rank >= k) return 0;
+        // Each granted position's entry is written right after its producer
+        // reserved it.  The group leader waits for it (bounded), takes it and
+        // clears the slot, then hands it to its group.
+        uint32_t val = 0;
+        if (lane == gbase) {
+            volatile uint32_t *slot = (volatile uint32_t *)&a.spq[(base + rank) & kSpillQueueMask];
+            for (int spin = 0; spin < kEntrySpinLimit; ++spin) {
+                val = *slot;
+                if (val) break;
+                __nanosleep(64);
+            }
+            if (val) {
+                *slot = 0u;
+            } else {
+                volatile uint32_t *d = a.done;
+                d[2 * a.n_slots] = 1u;  // error word: an entry never appeared
+                __threadfence_system();
+            }
+        }
+        val = __shfl_sync(gm, val, gbase);
+        if (val == 0) {
+            failed = true;
+            return -1;
+        }
+        const uint32_t entry = val - 1u;
+        task = entry & 0xffffffu;
+        gj = &a.slot_jobs[entry >> 24];
+        return 1;
+    }
+    __device__ __forceinline__ void idle() { __nanosleep(2000); }
+    __device__ __forceinline__ bool aborted() const
+    {
+        return *(volatile const unsigned int *)&a.ctl->abort != 0u;
+    }
+    __device__ __forceinline__ Ext open(const Job *gj, uint32_t task, Scoring &sc)
+    {
+        const Job J = ldcg_job(gj);
+        sc = J.sc;
+        return decode_cg(J, task);
+    }
+    __device__ __forceinline__ void retire(const Job *gj, uint32_t task, bool overflow, int32_t T,
+                                           int32_t bi, int32_t bj)
+    {
+        const Job J = ldcg_job(gj);
+        if (overflow) {
+            serve_list_wide(a, gj, J, task);
+        } else {
+            store_result_cg(J, task, T, bi, bj);
+            serve_count(a, gj, J);
+        }
+    }
+};
+
+template <int L1, int C1, int L2, int C2>
+__global__ void __launch_bounds__(256)
+serve_kernel(ServeArgs a, const uint32_t *pk, int64_t nw)
+{
+    const unsigned warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp_global % kSpillWarpEvery == kSpillWarpEvery - 1) {
+        SpillSrc src{a, 0, 0, false, false};  // second tier for the kernel's whole life
+        lockstep_loop<L2, C2>(src, pk, nw);
+        return;
+    }
+    for (;;) {
+        RingSrc src{a, 0ull, 0, 0, false};
+        lockstep_loop<L1, C1>(src, pk, nw);
+        if (__any_sync(FULL, src.leaving || src.aborted())) break;
+        // The second-tier backlog grew: drain it with the wider tile, then
+        // go back to the ring.
+        SpillSrc help{a, 0, 0, true, false};
+        lockstep_loop<L2, C2>(help, pk, nw);
+        if (__any_sync(FULL, help.failed || help.aborted())) break;
+    }
+    if ((threadIdx.x & 31) == 0) atomicSub(&a.ctl->ring_alive, 1u);
+}
+
+// Warps of a serving grid that run the first tier.
+__host__ __device__ inline uint32_t serve_ring_warps(int grid)
+{
+    const uint32_t total = (uint32_t)grid * 8u;
+    return total - total / kSpillWarpEvery;
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(256)
+lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_ptr,
+                uint32_t *counter, Spill spill)
+{
+    BatchSrc src{jp, order, *n_tasks_ptr, counter, spill};
+    lockstep_loop<L, C>(src, jp->packed, jp->n_words);
 }
 
 // ---------------------------------------------------------------------------

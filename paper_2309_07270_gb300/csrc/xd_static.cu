@@ -139,7 +139,7 @@ extern "C" int xdrop_align_static(const uint32_t *packed, uint64_t n_words,
     int64_t per_cta = (per_task + 63) / 64 * 64;
     int grid = (int)std::min<int64_t>(kStaticMaxCtas, kStaticScratchWords / per_cta);
     if (grid < 1) grid = 1, per_cta = kStaticScratchWords;
-    Job J;
+    Job J{};
     J.packed = packed;
     J.n_words = (int64_t)n_words;
     J.read_off = read_off;

@@ -60,4 +60,41 @@ cudaError_t launch_spill_mid(int grid, const Job *jp, Spill in, Spill out, cudaS
     return cudaGetLastError();
 }
 
+
+template <int L1, int C1, int L2, int C2>
+static cudaError_t serve_impl(int grid, const ServeArgs &a, const uint32_t *pk, int64_t nw,
+                              cudaStream_t s)
+{
+    (void)cudaGetLastError();
+    serve_kernel<L1, C1, L2, C2><<<grid, 256, 0, s>>>(a, pk, nw);
+    return cudaGetLastError();
+}
+
+template <int L1, int C1, int L2, int C2>
+static int serve_occupancy_impl()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, serve_kernel<L1, C1, L2, C2>, 256, 0);
+    return b;
+}
+
+cudaError_t launch_serve_mid(Tile t, int grid, const ServeArgs &a, const uint32_t *pk, int64_t nw,
+                           cudaStream_t s, bool *handled)
+{
+    *handled = true;
+    if (t.lanes == 8 && t.c == 16) return serve_impl<8, 16, 32, 16>(grid, a, pk, nw, s);
+    if (t.lanes == 16 && t.c == 8) return serve_impl<16, 8, 32, 16>(grid, a, pk, nw, s);
+    if (t.lanes == 32 && t.c == 4) return serve_impl<32, 4, 32, 16>(grid, a, pk, nw, s);
+    *handled = false;
+    return cudaSuccess;
+}
+
+int serve_occupancy_mid(Tile t)
+{
+    if (t.lanes == 8 && t.c == 16) return serve_occupancy_impl<8, 16, 32, 16>();
+    if (t.lanes == 16 && t.c == 8) return serve_occupancy_impl<16, 8, 32, 16>();
+    if (t.lanes == 32 && t.c == 4) return serve_occupancy_impl<32, 4, 32, 16>();
+    return -1;
+}
+
 }  // namespace xd

@@ -2,6 +2,7 @@
 // unbounded tier, validation and binning.
 #include "xd_launch.h"
 #include "xd_misc_kernels.cuh"
+#include "xd_serve.h"
 
 namespace xd {
 
@@ -79,6 +80,31 @@ int occupancy_narrow(Tile);
 int occupancy_mid(Tile);
 cudaError_t launch_window_plain(const Job *, uint32_t, uint32_t, Spill, cudaStream_t);
 cudaError_t launch_spill_mid(int, const Job *, Spill, Spill, cudaStream_t);
+
+cudaError_t launch_serve_narrow(Tile, int, const ServeArgs &, const uint32_t *, int64_t,
+                                cudaStream_t, bool *);
+cudaError_t launch_serve_mid(Tile, int, const ServeArgs &, const uint32_t *, int64_t, cudaStream_t,
+                             bool *);
+int serve_occupancy_narrow(Tile);
+int serve_occupancy_mid(Tile);
+
+cudaError_t launch_serve(Tile t, int grid, const ServeArgs &a, const uint32_t *pk, int64_t nw,
+                         cudaStream_t s)
+{
+    bool handled = false;
+    cudaError_t e = launch_serve_narrow(t, grid, a, pk, nw, s, &handled);
+    if (handled) return e;
+    e = launch_serve_mid(t, grid, a, pk, nw, s, &handled);
+    if (handled) return e;
+    return cudaErrorInvalidValue;
+}
+
+int serve_blocks_per_sm(Tile t)
+{
+    int b = serve_occupancy_narrow(t);
+    if (b < 0) b = serve_occupancy_mid(t);
+    return b;
+}
 
 const Tile kTiles[N_TILES] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4}, {32, 16}};
 

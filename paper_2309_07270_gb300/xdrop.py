@@ -23,6 +23,7 @@ XDROP_ETIMEDOUT = -4
 XDROP_EBUSY = -5
 XDROP_MODE_BATCHED = 0
 XDROP_MODE_PLAIN = 1
+XDROP_MODE_SERVE = 2
 XDROP_STATUS_OK = 0
 XDROP_STATUS_INVALID = 1
 XDROP_STATUS_TOO_LONG = 2
@@ -37,7 +38,8 @@ RESULT_DTYPE = np.dtype([("left_score", "<i4"), ("left_begin_a", "<i4"),
 EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_free", "xdrop_last_error", "xdrop_stream", "xdrop_get_stats",
            "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
-           "xdrop_align_static", "xdrop_static_last_error"]
+           "xdrop_align_static", "xdrop_static_last_error", "xdrop_load_reads",
+           "xdrop_submit_pairs", "xdrop_get_serve_stats"]
 
 
 class XdropError(RuntimeError):
@@ -57,6 +59,14 @@ class Stats(ctypes.Structure):
                 ("overflow_tasks", ctypes.c_uint64), ("wide_tasks", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("graph_replays", ctypes.c_uint32),
                 ("tile_lanes", ctypes.c_uint32), ("tile_cells", ctypes.c_uint32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_uint64), ("wide_passes", ctypes.c_uint64),
+                ("relaunches", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint64),
+                ("admission_waits", ctypes.c_uint64), ("published", ctypes.c_uint64),
+                ("consumed", ctypes.c_uint64), ("spill_reserved", ctypes.c_uint64),
+                ("spill_taken", ctypes.c_uint64), ("ring_warps", ctypes.c_uint64)]
 
 
 _lib = None
@@ -89,6 +99,12 @@ def load():
                                              ctypes.POINTER(Scoring), vp]
     lib.xdrop_last_spills.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     lib.xdrop_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.xdrop_load_reads.argtypes = [vp, vp, vp, vp, u32]
+    lib.xdrop_submit_pairs.argtypes = [vp, vp, sz, ctypes.POINTER(Scoring), vp,
+                                       ctypes.POINTER(u64)]
+    lib.xdrop_get_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
                                        u32, vp, vp]
     lib.xdrop_align_static.restype = ctypes.c_int
@@ -198,6 +214,32 @@ def xdrop_align_static(packed_ptr, n_words, read_off_ptr, read_len_ptr, n_reads,
 
 def xdrop_static_last_error() -> str:
     return load().xdrop_static_last_error().decode()
+
+
+def xdrop_load_reads(ctx, packed, read_off, read_len):
+    packed = np.ascontiguousarray(packed, dtype=np.uint32)
+    read_off = np.ascontiguousarray(read_off, dtype=np.uint64)
+    read_len = np.ascontiguousarray(read_len, dtype=np.uint32)
+    _check(load().xdrop_load_reads(ctx, _p(packed), _p(read_off), _p(read_len), len(read_len)),
+           ctx)
+
+
+def xdrop_submit_pairs(ctx, pairs, sc: Scoring, out):
+    """Host pairs against the resident reads; ``out`` (RESULT_DTYPE) must
+    stay alive until xdrop_sync returns."""
+    pairs = np.ascontiguousarray(pairs)
+    if pairs.dtype.itemsize != 20 or out.dtype.itemsize != 28 or not out.flags.c_contiguous:
+        raise TypeError("pairs must be 20-byte records and out a contiguous 28-byte-record array")
+    t = ctypes.c_uint64()
+    _check(load().xdrop_submit_pairs(ctx, _p(pairs), len(pairs), ctypes.byref(sc), _p(out),
+                                     ctypes.byref(t)), ctx)
+    return t.value
+
+
+def xdrop_get_serve_stats(ctx) -> dict:
+    st = ServeStats()
+    _check(load().xdrop_get_serve_stats(ctx, ctypes.byref(st)), ctx)
+    return {k: getattr(st, k) for k, _ in ServeStats._fields_}
 
 
 def xdrop_set_tile(ctx, lanes, cells):

@@ -1,0 +1,180 @@
+"""Serving (continuous batching) on the GPU.
+
+Requests of read pairs from 25 producer threads go to one persistent
+serving kernel.  Each request's results must be identical (integers,
+tolerance 0) whether it runs alone or in the mix, and equal to the oracle.
+Memory admission must queue requests that do not fit the budget and refuse
+one that never can.  Extensions whose band outgrows the serving tile must
+go through the wider tiers and stay exact.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2309_07270_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_07270_gb300 import build, xdrop
+    build.build()
+    return xdrop
+
+
+@pytest.fixture(scope="module")
+def pool():
+    """A small genome-overlap pool (1 Mbp genome, 29x)."""
+    return W.genome_overlaps(genome_len=1_000_000, seed=5)
+
+
+def requests_for(pool, n_producers=25, per_producer=3, lo=50, hi=600, seed=100):
+    reqs = []
+    for p in range(n_producers):
+        rng = np.random.Generator(np.random.PCG64(seed + p))
+        for _ in range(per_producer):
+            k = int(rng.integers(lo, hi + 1))
+            reqs.append((p, rng.integers(0, pool.n_pairs, size=k)))
+    return reqs
+
+
+def serve_ctx(X, pool, budget=0, tile=None):
+    ctx = X.xdrop_init(0, budget, X.XDROP_MODE_SERVE)
+    if tile:
+        X.xdrop_set_tile(ctx, *tile)
+    X.xdrop_load_reads(ctx, pool.packed, pool.read_off, pool.read_len)
+    return ctx
+
+
+SYNC_NS = int(60e9)  # a request that takes longer fails the test with the loop's counters
+
+
+def sync(X, ctx, t):
+    try:
+        X.xdrop_sync(ctx, t, SYNC_NS)
+    except X.XdropError as e:
+        raise AssertionError(f"{e}; serving counters {X.xdrop_get_serve_stats(ctx)}") from e
+
+
+def run_alone(X, ctx, pool, reqs, sc):
+    outs = []
+    for _, idx in reqs:
+        out = np.zeros(len(idx), X.RESULT_DTYPE)
+        t = X.xdrop_submit_pairs(ctx, pool.pairs[idx], sc, out)
+        sync(X, ctx, t)
+        outs.append(out)
+    return outs
+
+
+def run_mix(X, ctx, pool, reqs, sc, n_producers=25):
+    """Every producer thread submits all its requests back to back, then
+    syncs them; all producers run at once."""
+    outs = [None] * len(reqs)
+    errors = []
+    by_prod = {}
+    for i, (p, idx) in enumerate(reqs):
+        by_prod.setdefault(p, []).append(i)
+
+    def producer(items):
+        try:
+            tickets = []
+            for i in items:
+                out = np.zeros(len(reqs[i][1]), X.RESULT_DTYPE)
+                outs[i] = out
+                tickets.append(X.xdrop_submit_pairs(ctx, pool.pairs[reqs[i][1]], sc, out))
+                time.sleep(0.001)
+            for t in tickets:
+                sync(X, ctx, t)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    th = [threading.Thread(target=producer, args=(items,)) for items in by_prod.values()]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errors, errors
+    assert all(not t.is_alive() for t in th)
+    return outs
+
+
+def test_alone_equals_mix_equals_oracle(X, orc, pool):
+    reqs = requests_for(pool)
+    sc = X.scoring(1, -1, -1, 50)
+    ctx = serve_ctx(X, pool)
+    try:
+        alone = run_alone(X, ctx, pool, reqs, sc)
+        mix = run_mix(X, ctx, pool, reqs, sc)
+        st = X.xdrop_get_serve_stats(ctx)
+    finally:
+        X.xdrop_free(ctx)
+    for a, b in zip(alone, mix):
+        assert np.array_equal(a.view(np.int32), b.view(np.int32))
+    assert st["requests_done"] == 2 * len(reqs)
+    assert st["max_in_flight"] > 1  # requests overlapped on the device
+    # oracle on a sample of requests
+    for k in range(0, len(reqs), 9):
+        idx = reqs[k][1]
+        want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
+                               1, -1, -1, 50, nthreads=8)
+        assert np.array_equal(alone[k].view(np.int32), want.view(np.int32))
+
+
+def test_memory_admission_queues_and_refuses(X, orc, pool):
+    reqs = requests_for(pool, n_producers=6, per_producer=3, lo=200, hi=400, seed=300)
+    sc = X.scoring(1, -1, -1, 50)
+    budget = 64 * 1024  # two or three requests' buffers at a time
+    ctx = serve_ctx(X, pool, budget=budget)
+    try:
+        mix = run_mix(X, ctx, pool, reqs, sc, n_producers=6)
+        st = X.xdrop_get_serve_stats(ctx)
+        big = pool.pairs[: 5000]
+        out = np.zeros(len(big), X.RESULT_DTYPE)
+        with pytest.raises(X.XdropError) as ei:
+            X.xdrop_submit_pairs(ctx, big, sc, out)
+        assert ei.value.code == X.XDROP_ENOMEM
+    finally:
+        X.xdrop_free(ctx)
+    assert st["admission_waits"] > 0
+    assert st["max_in_flight"] <= 3
+    for k in (0, len(reqs) - 1):
+        want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[reqs[k][1]],
+                               1, -1, -1, 50, nthreads=8)
+        assert np.array_equal(mix[k].view(np.int32), want.view(np.int32))
+
+
+def test_overflowing_bands_take_wider_tiers(X, orc, pool):
+    """X = 400 makes bands wider than both in-kernel tiers (64 and 128
+    slots): they finish on the 512-slot and unbounded tiers."""
+    reqs = requests_for(pool, n_producers=4, per_producer=2, lo=20, hi=60, seed=500)
+    sc = X.scoring(1, -1, -1, 400)
+    ctx = serve_ctx(X, pool, tile=(4, 16))
+    try:
+        mix = run_mix(X, ctx, pool, reqs, sc, n_producers=4)
+        st = X.xdrop_get_serve_stats(ctx)
+    finally:
+        X.xdrop_free(ctx)
+    assert st["wide_passes"] > 0
+    for k, (_, idx) in enumerate(reqs):
+        want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
+                               1, -1, -1, 400, nthreads=8)
+        assert np.array_equal(mix[k].view(np.int32), want.view(np.int32))
+
+
+def test_submit_pairs_outside_serving(X, orc, pool):
+    """xdrop_submit_pairs in batched mode runs an ordinary ticket."""
+    with X.Aligner() as al:
+        X.xdrop_load_reads(al.ctx, pool.packed, pool.read_off, pool.read_len)
+        idx = np.arange(0, pool.n_pairs, 37)
+        out = np.zeros(len(idx), X.RESULT_DTYPE)
+        t = X.xdrop_submit_pairs(al.ctx, pool.pairs[idx], X.scoring(1, -1, -1, 50), out)
+        X.xdrop_sync(al.ctx, t, SYNC_NS)
+    want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
+                           1, -1, -1, 50, nthreads=8)
+    assert np.array_equal(out.view(np.int32), want.view(np.int32))
