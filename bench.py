@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--x", type=int, default=50)
+    ap.add_argument("--workload", default="genome29x",
+                    choices=["genome29x", "uneven", "genome100x"],
+                    help="genome29x (default, the headline), uneven (1M Pareto-length pairs), "
+                         "genome100x (100x coverage)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -77,17 +81,29 @@ def max_over_ranks(value, device):
     return float(t.item())
 
 
-def workload(x, pairs=0):
+WORKLOAD_NAME = {"genome29x": "genome-29x-overlaps", "uneven": "uneven-pareto-1M-pairs",
+                 "genome100x": "genome-100x-overlaps"}
+
+
+def workload(x, pairs=0, kind="genome29x"):
     import numpy as np
     from paper_2309_07270_gb300 import workloads as W
-    w = W.genome_overlaps(seed=1, x=x)
+    if kind == "uneven":
+        w = W.uneven_pairs(n_pairs=1_000_000, seed=3, x=x)
+        w.meta.update(genome_len=None, coverage=None, mean_len=None, sd_len=None, seed=3)
+    elif kind == "genome100x":
+        w = W.genome_overlaps(coverage=100.0, seed=4, x=x)
+    else:
+        w = W.genome_overlaps(seed=1, x=x)
+    w.meta["kind"] = kind
     if pairs and pairs < w.n_pairs:
         w = w.subset(np.arange(pairs))
     return w
 
 
 def workload_config(w):
-    return {"workload": "genome-29x-overlaps", "genome_bp": w.meta["genome_len"],
+    return {"workload": WORKLOAD_NAME[w.meta.get("kind", "genome29x")],
+            "genome_bp": w.meta["genome_len"],
             "coverage": w.meta["coverage"], "reads": w.n_reads, "pairs": w.n_pairs,
             "extensions": 2 * w.n_pairs, "read_len_mean": w.meta["mean_len"],
             "read_len_sd": w.meta["sd_len"], "error_rate": 0.12, "seed_len": 17,
@@ -131,7 +147,7 @@ def run_reference(args):
     import numpy as np
     import oracle
     oracle.build()
-    w = workload(args.x, args.pairs)
+    w = workload(args.x, args.pairs, args.workload)
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(1234)
     per_step_pairs = 1500
@@ -280,7 +296,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    w = workload(args.x, args.pairs)
+    w = workload(args.x, args.pairs, args.workload)
     sc = X.scoring(w.match, w.mismatch, w.gap, w.x)
     dev = X.DeviceInputs.from_workload(w, device=dev_name)
     batched = X.Aligner(device=local, mode=X.XDROP_MODE_BATCHED)
@@ -433,7 +449,7 @@ def run_serve_sweep(args):
     from paper_2309_07270_gb300 import build as B
     from paper_2309_07270_gb300 import xdrop as X
     B.build()
-    w = workload(args.x, args.pairs)
+    w = workload(args.x, args.pairs, args.workload)
     sc = X.scoring(w.match, w.mismatch, w.gap, w.x)
     dev = X.DeviceInputs.from_workload(w)
     with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:

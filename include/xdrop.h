@@ -103,6 +103,7 @@ typedef struct {
     uint32_t graph_replays;  /* CUDA graph launches of that ticket        */
     uint32_t tile_lanes;     /* first band tier: lanes per extension      */
     uint32_t tile_cells;     /* first band tier: cells per lane           */
+    uint64_t device_bytes;   /* device memory the context holds now       */
 } xdrop_stats;
 
 typedef struct {
@@ -162,7 +163,10 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
                      const uint32_t *read_len, uint32_t n_reads);
 
 /* Align n_pairs pairs (HOST memory, copied before return) against the
- * resident read set.  Results go to `out` (host memory, valid until the
+ * resident read set.  In batched mode with a device memory budget too small
+ * for the whole pair table, the pairs stream through in chunks sized to the
+ * budget, each one a replay of the same CUDA graph (xdrop_stats counts them
+ * as graph_replays); XDROP_ENOMEM if not even a 1,024-pair chunk fits.  Results go to `out` (host memory, valid until the
  * ticket's sync returns XDROP_OK).  Pairs are validated first
  * (XDROP_EINVAL, nothing queued).
  *

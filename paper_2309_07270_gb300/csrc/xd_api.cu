@@ -395,12 +395,59 @@ int launch_ticket(xdrop_ctx *c, Ticket *tk, const Job &job, uint32_t maxlen)
     return XDROP_OK;
 }
 
-int new_ticket(xdrop_ctx *c, size_t n_pairs, bool device_submit, Ticket **out)
+// Batched mode over resident reads when the pair table does not fit the
+// device memory budget: the pairs stream through in chunks of `chunk`
+// pairs (host -> device, one replay of the same CUDA graph, results back),
+// all in stream order on the context's stream.  tk->h_job has one pinned
+// Job slot per chunk, so every chunk's descriptor copy has its own source.
+int launch_ticket_chunked(xdrop_ctx *c, Ticket *tk, const xdrop_pair *h_pairs, size_t n_pairs,
+                          size_t chunk, const Job &base, char *d_pairs, char *d_out,
+                          uint32_t maxlen)
+{
+    cudaStream_t s = c->stream;
+    int rc;
+    if ((rc = ensure_scratch(c, 2 * chunk, maxlen))) return rc;
+    CK(cudaEventRecord(tk->ev_begin, s));
+    size_t k = 0;
+    for (size_t p0 = 0; p0 < n_pairs; p0 += chunk, ++k) {
+        const size_t np = std::min(chunk, n_pairs - p0);
+        CK(cudaMemcpyAsync(d_pairs, h_pairs + p0, np * sizeof(xdrop_pair), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(d_out, 0, np * sizeof(xdrop_result), s));
+        Job job = base;
+        job.pairs = (const Pair *)d_pairs;
+        job.n_pairs = np;
+        job.out = (int32_t *)d_out;
+        tk->h_job[k] = job;
+        CK(cudaMemcpyAsync(c->d_job, &tk->h_job[k], sizeof(Job), cudaMemcpyHostToDevice, s));
+        if (k == 0) {  // first tile: as for an unchunked submit
+            Tile t = c->forced;
+            if (!t.lanes) {
+                auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x);
+                auto it = c->tuned.find(key);
+                if (it == c->tuned.end()) {
+                    if ((rc = autotune(c, tk, job, &t))) return rc;
+                    c->tuned[key] = t;
+                } else {
+                    t = it->second;
+                }
+            }
+            c->tile0 = t;
+        }
+        if ((rc = run_batched(c, tk))) return rc;
+        CK(cudaMemcpyAsync(tk->h_out + p0, d_out, np * sizeof(xdrop_result), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(tk->ev_end, s));
+    CK(cudaMemcpyAsync(tk->h_ctrs, c->d_ctrs, C_WORDS * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(tk->ev_done, s));
+    return XDROP_OK;
+}
+
+int new_ticket(xdrop_ctx *c, size_t n_pairs, bool device_submit, Ticket **out, size_t n_jobs = 1)
 {
     Ticket *tk = new Ticket();
     tk->device_submit = device_submit;
     tk->n_pairs = n_pairs;
-    size_t pin = align_up(sizeof(Job)) + align_up(C_WORDS * 4) +
+    size_t pin = align_up(sizeof(Job) * std::max<size_t>(n_jobs, 1)) + align_up(C_WORDS * 4) +
                  (device_submit ? 0 : align_up(n_pairs * sizeof(xdrop_result)));
     cudaError_t e = cudaHostAlloc(&tk->h_pinned, pin, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreate(&tk->ev_begin);
@@ -412,7 +459,7 @@ int new_ticket(xdrop_ctx *c, size_t n_pairs, bool device_submit, Ticket **out)
     }
     char *p = (char *)tk->h_pinned;
     tk->h_job = (Job *)p;
-    p += align_up(sizeof(Job));
+    p += align_up(sizeof(Job) * std::max<size_t>(n_jobs, 1));
     tk->h_ctrs = (uint32_t *)p;
     p += align_up(C_WORDS * 4);
     tk->h_out = device_submit ? nullptr : (xdrop_result *)p;
@@ -690,6 +737,7 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st)
     if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
     *st = c->last;
+    st->device_bytes = c->used;
     return XDROP_OK;
 }
 
@@ -776,15 +824,43 @@ int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
         *t = id | kServeTicket;
         return XDROP_OK;
     }
-    // not serving: an ordinary ticket over the resident reads
+    // not serving: an ordinary ticket over the resident reads, streamed in
+    // chunks when the pair table does not fit the device memory budget
     std::lock_guard<std::mutex> lk(c->mu);
     CK(cudaSetDevice(c->device));
+    const size_t per_pair = sizeof(xdrop_pair) + sizeof(xdrop_result) + 2 * 4 * 4;  // + task scratch
+    size_t chunk = std::max<size_t>(n_pairs, 1);
+    if (c->budget && c->mode != XDROP_MODE_PLAIN) {
+        const size_t scratch_now = c->order.cap + c->spill[0].cap + c->spill[1].cap + c->spill[2].cap;
+        const size_t fixed = c->used - scratch_now + 4 * kAlign;
+        if (c->budget <= fixed + 1024 * per_pair)
+            return fail(c->tickets.empty() ? XDROP_ENOMEM : XDROP_EBUSY,
+                        "device memory budget too small for resident reads plus a chunk");
+        if (!c->tickets.empty() && c->budget < c->used + chunk * per_pair)
+            return fail(XDROP_EBUSY, "device memory budget taken by work in flight");
+        const size_t fit = (c->budget - fixed) / per_pair;
+        if (fit < chunk) {
+            chunk = fit;
+            // scratch sized for this chunk must not stay larger from before
+            for (DevBuf *b : {&c->order, &c->spill[0], &c->spill[1], &c->spill[2]}) {
+                if (b->cap > 2 * chunk * 4) {
+                    CK(cudaStreamSynchronize(c->stream));
+                    cudaFree(b->p);
+                    c->used -= b->cap;
+                    b->p = nullptr;
+                    b->cap = 0;
+                    c->scratch_version += 1;
+                }
+            }
+        }
+    }
+    const size_t n_chunks = (std::max<size_t>(n_pairs, 1) + chunk - 1) / chunk;
     Ticket *tk = nullptr;
-    if ((rc = new_ticket(c, n_pairs, false, &tk))) return rc;
+    if ((rc = new_ticket(c, n_pairs, false, &tk, n_chunks))) return rc;
     tk->out = out;
-    const size_t o_out = align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_pair));
-    const size_t bytes = o_out + align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_result));
-    if (c->budget && c->used + bytes > c->budget) {
+    const size_t o_out = align_up(chunk * sizeof(xdrop_pair));
+    const size_t bytes = o_out + align_up(chunk * sizeof(xdrop_result));
+    if (c->budget && c->mode == XDROP_MODE_PLAIN && c->used + bytes > c->budget) {
         free_ticket(c, tk);
         return fail(c->tickets.empty() ? XDROP_ENOMEM : XDROP_EBUSY,
                     "device memory budget exceeded (%zu bytes needed)", bytes);
@@ -797,6 +873,25 @@ int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
     tk->d_bytes = bytes;
     c->used += bytes;
     char *d = (char *)tk->d_mem;
+    if (n_chunks > 1) {
+        Job base{};
+        base.packed = (const uint32_t *)c->r_packed.p;
+        base.n_words = (int64_t)c->r_words;
+        base.read_off = (const uint64_t *)c->r_off.p;
+        base.read_len = (const uint32_t *)c->r_len.p;
+        base.n_reads = c->r_n;
+        base.sc = sc;
+        if ((rc = launch_ticket_chunked(c, tk, pairs, n_pairs, chunk, base, d, d + o_out,
+                                        c->r_maxlen))) {
+            cudaStreamSynchronize(c->stream);
+            free_ticket(c, tk);
+            return rc;
+        }
+        tk->id = c->next_id++;
+        c->tickets[tk->id] = tk;
+        *t = tk->id;
+        return XDROP_OK;
+    }
     if (n_pairs) e = cudaMemcpyAsync(d, pairs, n_pairs * sizeof(xdrop_pair), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && n_pairs)
         e = cudaMemsetAsync(d + o_out, 0, n_pairs * sizeof(xdrop_result), c->stream);

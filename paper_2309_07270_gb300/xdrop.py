@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("tasks", ctypes.c_uint64),
                 ("overflow_tasks", ctypes.c_uint64), ("wide_tasks", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("graph_replays", ctypes.c_uint32),
-                ("tile_lanes", ctypes.c_uint32), ("tile_cells", ctypes.c_uint32)]
+                ("tile_lanes", ctypes.c_uint32), ("tile_cells", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64)]
 
 
 class ServeStats(ctypes.Structure):
