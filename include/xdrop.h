@@ -102,7 +102,8 @@ typedef struct {
     uint32_t launches;       /* kernel launches of that ticket            */
     uint32_t graph_replays;  /* CUDA graph launches of that ticket        */
     uint32_t tile_lanes;     /* first band tier: lanes per extension      */
-    uint32_t tile_cells;     /* first band tier: cells per lane           */
+    uint32_t tile_cells;     /* first band tier: cells per lane, with
+                                XDROP_TILE_PACKED16 set for a packed tile */
     uint64_t device_bytes;   /* device memory the context holds now       */
 } xdrop_stats;
 
@@ -200,12 +201,20 @@ void *xdrop_stream(xdrop_ctx *c);
 /* Statistics of the most recently synced ticket. */
 int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
 
+/* Packed tiles: 16-bit cells, two per 32-bit register, for scorings with
+ * match <= 1024, mismatch >= -1024, gap >= -1024 and x + match <= 2046
+ * (results identical to the 32-bit tiles; other scorings run the 32-bit
+ * tile of the same shape).  Set in `cells` of xdrop_set_tile. */
+#define XDROP_TILE_PACKED16 0x100
+
 /* Batched mode: fix the first band tier to `lanes` lanes per extension
  * and `cells` cells per lane (lanes*cells slots per anti-diagonal parity),
  * or pass lanes = 0 to go back to autotuning.  Autotuning (the default)
  * times every first-tier tile on a sample of the first submit with a new
  * scoring and keeps the fastest for that scoring.  Tiles: 4x16, 8x8, 16x4,
- * 8x16, 16x8, 32x4.  Returns XDROP_EINVAL for another shape. */
+ * 8x16, 16x8, 32x4, and packed (cells | XDROP_TILE_PACKED16) 4x16, 8x8,
+ * 8x16, 16x8.  Returns XDROP_EINVAL for another shape.  Serving mode uses
+ * the 32-bit tile of a packed shape. */
 int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells);
 
 /* Task ids (2*pair + 1 for a right extension, 2*pair for a left one)

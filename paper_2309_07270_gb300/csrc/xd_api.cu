@@ -247,8 +247,14 @@ int enqueue_batched(xdrop_ctx *c, Tile t0, int bps, bool main_events, uint32_t *
     return XDROP_OK;
 }
 
-// Candidate first tiles for autotuning (all persistent instantiations).
+// Candidate first tiles for autotuning (all persistent instantiations);
+// the packed 16-bit ones only for scorings they hold exactly.
 const Tile kTuneTiles[] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4}};
+const Tile kPackedTiles[] = {{4, 16, true}, {8, 8, true}, {8, 16, true}, {16, 8, true}};
+
+// The first tile for a submit: the forced one (unpacked when the scoring
+// does not fit 16 bits) or the tuned one for this scoring.
+int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out);
 
 // Time the whole batched sequence for every candidate first tile on a
 // sample of `job` (its first pairs), pick the fastest.  Synchronous.
@@ -265,7 +271,9 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     *best = Tile{0, 0};
-    for (const Tile &t : kTuneTiles) {
+    std::vector<Tile> cands(std::begin(kTuneTiles), std::end(kTuneTiles));
+    if (packed_scoring_ok(job.sc)) cands.insert(cands.end(), std::begin(kPackedTiles), std::end(kPackedTiles));
+    for (const Tile &t : cands) {
         const int bps = persistent_blocks_per_sm(t);
         if (bps <= 0) continue;
         float tmin = 1e30f;
@@ -290,10 +298,31 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     return best->lanes ? XDROP_OK : fail(XDROP_ECUDA, "no tile could be timed");
 }
 
+int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out)
+{
+    Tile t = c->forced;
+    if (t.lanes) {
+        if (t.packed && !packed_scoring_ok(job.sc)) t.packed = false;
+        *out = t;
+        return XDROP_OK;
+    }
+    auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x);
+    auto it = c->tuned.find(key);
+    if (it != c->tuned.end()) {
+        *out = it->second;
+        return XDROP_OK;
+    }
+    int rc = autotune(c, tk, job, &t);
+    if (rc) return rc;
+    c->tuned[key] = t;
+    *out = t;
+    return XDROP_OK;
+}
+
 int run_batched(xdrop_ctx *c, Ticket *tk)
 {
     if (!c->gexec || c->graph_version != c->scratch_version ||
-        c->graph_tile.lanes != c->tile0.lanes || c->graph_tile.c != c->tile0.c) {
+        !c->graph_tile.same(c->tile0)) {
         c->tile0_bps = persistent_blocks_per_sm(c->tile0);
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -368,18 +397,7 @@ int launch_ticket(xdrop_ctx *c, Ticket *tk, const Job &job, uint32_t maxlen)
         tk->launches += 1;
     }
     if (job.n_pairs && c->mode != XDROP_MODE_PLAIN) {
-        Tile t = c->forced;
-        if (!t.lanes) {
-            auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x);
-            auto it = c->tuned.find(key);
-            if (it == c->tuned.end()) {
-                if ((rc = autotune(c, tk, job, &t))) return rc;
-                c->tuned[key] = t;
-            } else {
-                t = it->second;
-            }
-        }
-        c->tile0 = t;
+        if ((rc = pick_tile(c, tk, job, &c->tile0))) return rc;
     }
     if (job.n_pairs) {
         if (c->mode == XDROP_MODE_PLAIN) rc = run_plain(c, tk, job.n_pairs);
@@ -420,18 +438,7 @@ int launch_ticket_chunked(xdrop_ctx *c, Ticket *tk, const xdrop_pair *h_pairs, s
         tk->h_job[k] = job;
         CK(cudaMemcpyAsync(c->d_job, &tk->h_job[k], sizeof(Job), cudaMemcpyHostToDevice, s));
         if (k == 0) {  // first tile: as for an unchunked submit
-            Tile t = c->forced;
-            if (!t.lanes) {
-                auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x);
-                auto it = c->tuned.find(key);
-                if (it == c->tuned.end()) {
-                    if ((rc = autotune(c, tk, job, &t))) return rc;
-                    c->tuned[key] = t;
-                } else {
-                    t = it->second;
-                }
-            }
-            c->tile0 = t;
+            if ((rc = pick_tile(c, tk, job, &c->tile0))) return rc;
         }
         if ((rc = run_batched(c, tk))) return rc;
         CK(cudaMemcpyAsync(tk->h_out + p0, d_out, np * sizeof(xdrop_result), cudaMemcpyDeviceToHost, s));
@@ -693,7 +700,9 @@ int xdrop_sync(xdrop_ctx *c, xdrop_ticket t, int64_t timeout_ns)
     st.launches = tk->launches;
     st.graph_replays = tk->graph_replays;
     st.tile_lanes = c->mode == XDROP_MODE_PLAIN ? 32 : c->tile0.lanes;
-    st.tile_cells = c->mode == XDROP_MODE_PLAIN ? 4 : c->tile0.c;
+    st.tile_cells = c->mode == XDROP_MODE_PLAIN
+                        ? 4
+                        : c->tile0.c | (c->tile0.packed ? XDROP_TILE_PACKED16 : 0);
     c->last = st;
     const uint32_t nbad = tk->device_submit ? tk->h_ctrs[C_NBAD] : 0;
     free_ticket(c, tk);
@@ -787,7 +796,8 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
         rr.read_len = (const uint32_t *)c->r_len.p;
         rr.n_reads = n_reads;
         std::string err;
-        const Tile t = c->forced.lanes ? c->forced : Tile{4, 16};
+        Tile t = c->forced.lanes ? c->forced : Tile{4, 16};
+        t.packed = false;  // the serving kernel has 32-bit tiles only
         c->srv = xd::server_create(c->device, c->sm_count, c->budget, t, rr, c->h_len.data(),
                                    (int32_t *)c->wide.p, c->wide_per_cta, c->wide_grid, err);
         if (!c->srv) return fail(XDROP_ECUDA, "%s", err.c_str());
@@ -950,12 +960,22 @@ int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells)
         c->forced = Tile{0, 0};
         return XDROP_OK;
     }
-    for (const Tile &t : kTuneTiles)
-        if (t.lanes == lanes && t.c == cells) {
-            c->forced = t;
-            return XDROP_OK;
-        }
-    return fail(XDROP_EINVAL, "no %dx%d tile", lanes, cells);
+    const bool packed = (cells & XDROP_TILE_PACKED16) != 0;
+    cells &= ~XDROP_TILE_PACKED16;
+    if (packed) {
+        for (const Tile &t : kPackedTiles)
+            if (t.lanes == lanes && t.c == cells) {
+                c->forced = t;
+                return XDROP_OK;
+            }
+    } else {
+        for (const Tile &t : kTuneTiles)
+            if (t.lanes == lanes && t.c == cells) {
+                c->forced = t;
+                return XDROP_OK;
+            }
+    }
+    return fail(XDROP_EINVAL, "no %dx%d%s tile", lanes, cells, packed ? " packed" : "");
 }
 
 int xdrop_last_spills(xdrop_ctx *c, uint32_t *dst, size_t cap, size_t *n)

@@ -9,9 +9,11 @@
 namespace xd {
 
 struct Tile {
-    int lanes;  // lanes per extension (4, 8, 16 or 32)
-    int c;      // cells per lane per diagonal
+    int lanes;            // lanes per extension (4, 8, 16 or 32)
+    int c;                // cells per lane per diagonal
+    bool packed = false;  // 16-bit cells, two per register (xd_lockstep16.cuh)
     int width() const { return lanes * c; }
+    bool same(const Tile &o) const { return lanes == o.lanes && c == o.c && packed == o.packed; }
 };
 
 // Band tiles the library is built with, narrowest first.
@@ -32,6 +34,8 @@ cudaError_t launch_spill(Tile t, bool count, int grid, const Job *jp, Spill in, 
                          cudaStream_t s);
 // Blocks per SM of a persistent tile at 256 threads per block.
 int persistent_blocks_per_sm(Tile t);
+// Whether a scoring fits the packed 16-bit tiles exactly.
+bool packed_scoring_ok(const Scoring &sc);
 
 cudaError_t launch_wide(bool count, int grid, const Job *jp, Spill in, int32_t *scratch,
                         int64_t scratch_per_cta, cudaStream_t s);

@@ -1,0 +1,367 @@
+// Packed 16-bit lockstep band kernel: two window slots per 32-bit register.
+//
+// Same extension, same reading of the X-drop recurrence and the same
+// results as lockstep_loop (xd_device.cuh); only the arithmetic changes.
+// It is exact whenever the scoring passes packed16_ok():
+//   match <= 1024, mismatch >= -1024, gap >= -1024, x + match <= 2046.
+//
+// Normalised scores.  A cell on anti-diagonal d is stored as
+//   r = H + x + d*|gap| - B
+// (B = the multiples of kRebase taken off so far).  Then the two gap
+// predecessors enter unchanged and the diagonal one with s + 2|gap|:
+//   r(d) = max(r_diag(d-2) + s + 2|gap|,  r_up(d-1),  r_left(d-1)),
+// one DPX max and one DPX add-max per register (two cells).  The
+// threshold of diagonal d (T of d-1 minus x) becomes thr = T + d*|gap| - B,
+// a cell is live iff r >= thr, and x_rel = r - thr <= x + match < 2047.
+//
+// Layout.  Lane g of a group of L lanes holds the window slots g*S .. g*S+S-1
+// (S = 2*C2 slots).  Register t holds slot t in its low half and slot t+C2
+// in its high half, so the neighbour slot s+1 (s-1) of every slot in
+// register t sits in register t+1 (t-1) at the same half; only the end
+// registers need a byte permute and one shuffle per diagonal.
+//
+// Ranges (no 16-bit wrap anywhere): dead slots hold kDead = -12288; thr
+// stays in [0, 8192) because every odd diagonal subtracts kRebase from the
+// frame once thr reaches kRebase and thr grows by at most 2*(match+|gap|)
+// <= 4096 per diagonal pair; live values stay below 8192 + 2047; a value
+// built from dead predecessors stays below kDead + match + 2|gap| < 0; the
+// relative value r - thr stays above -21504.
+//
+// Best cell.  The key of a slot is max(r - thr, -1) * 16 + (S-1-slot) in
+// 16 bits; the lane's best key becomes value * 512 + (31 - lane) * 16 +
+// (S-1-slot) in 32 bits, so one group max gives the largest value and,
+// among equal values, the lowest window slot (lane first, then slot), i.e.
+// the first cell in order of increasing i on the diagonal.
+#pragma once
+#include "xd_device.cuh"
+
+namespace xd {
+
+namespace p16 {
+
+constexpr int32_t kDead = -12288;
+constexpr uint32_t kDead2 = 0xD000D000u;  // kDead in both halves
+constexpr int32_t kRebase = 4096;
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack2(int32_t v) { return ((uint32_t)v & 0xFFFFu) * 0x10001u; }
+
+// Byte-permute selector giving 0xFFFF in the low half where slot t's match
+// bit is set and likewise in the high half for slot t+C2.  Match bits sit
+// at the msb of byte (s >> 2) of R[s & 3] (see dp16); msb-replicating
+// selectors (8 | byte) turn them into half-word masks.
+template <int C2>
+__host__ __device__ constexpr uint32_t mask_sel(int t)
+{
+    return (uint32_t)((8 | (t >> 2)) | ((8 | (t >> 2)) << 4) | ((8 | ((t + C2) >> 2)) << 8) |
+                      ((8 | ((t + C2) >> 2)) << 12));
+}
+
+template <int C2>
+__host__ __device__ constexpr uint32_t idx2(int t)
+{
+    return (uint32_t)(2 * C2 - 1 - t) | ((uint32_t)(2 * C2 - 1 - (t + C2)) << 16);
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t tree_max2(const uint32_t (&k)[N])
+{
+    if constexpr (N == 1) {
+        return k[0];
+    } else if constexpr (N == 2) {
+        return __vmaxs2(k[0], k[1]);
+    } else {
+        constexpr int M = (N + 2) / 3;
+        uint32_t r[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (3 * i + 2 < N) r[i] = __vimax3_s16x2(k[3 * i], k[3 * i + 1], k[3 * i + 2]);
+            else if (3 * i + 1 < N) r[i] = __vmaxs2(k[3 * i], k[3 * i + 1]);
+            else r[i] = k[3 * i];
+        }
+        return tree_max2<M>(r);
+    }
+}
+
+// One anti-diagonal for one lane: V (diagonal d-2, overwritten with d) and
+// U (d-1).  edge: the neighbouring lane's end register of U (next lane's
+// register 0 on odd diagonals, previous lane's register C2-1 on even ones).
+// Returns the lane's 16-bit key, sign-extended.
+template <int C2, bool ODD, bool MASKED>
+__device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
+                                        uint32_t edge, uint32_t eq, uint32_t ma2, uint32_t mi2,
+                                        uint32_t nthr2, int32_t i0, int32_t j0, int32_t m,
+                                        int32_t n)
+{
+    const uint32_t R[4] = {eq << 7, eq << 5, eq << 3, eq << 1};
+    uint32_t key[C2];
+#pragma unroll
+    for (int t = 0; t < C2; ++t) {
+        uint32_t sh;
+        if (ODD) sh = (t + 1 < C2) ? U[t + 1] : prmt(U[0], edge, 0x5432);
+        else sh = (t > 0) ? U[t - 1] : prmt(edge, U[C2 - 1], 0x5432);
+        const uint32_t nb = __vmaxs2(U[t], sh);
+        const uint32_t mk = prmt(R[t & 3], R[t & 3], mask_sel<C2>(t));
+        const uint32_t s2 = (mk & ma2) | (~mk & mi2);
+        uint32_t r = __viaddmax_s16x2(V[t], s2, nb);
+        if (MASKED) {
+            if (i0 + t > m || j0 - t > n) r = (r & 0xFFFF0000u) | (kDead2 & 0xFFFFu);
+            if (i0 + t + C2 > m || j0 - t - C2 > n) r = (r & 0xFFFFu) | (kDead2 & 0xFFFF0000u);
+        }
+        const uint32_t x = __viaddmax_s16x2(r, nthr2, 0xFFFFFFFFu);  // max(r - thr, -1)
+        const uint32_t pm = prmt(x, x, 0xBB99);                      // 0xFFFF where dead
+        V[t] = (r & ~pm) | (kDead2 & pm);
+        key[t] = ((x << 4) & 0xFFF0FFF0u) | idx2<C2>(t);
+    }
+    const uint32_t kk = tree_max2<C2>(key);
+    const int32_t hi = (int32_t)kk >> 16;
+    const int32_t lo = (int32_t)prmt(kk, 0u, 0x9910);  // sign-extended low half
+    return hi > lo ? hi : lo;
+}
+
+}  // namespace p16
+
+__host__ __device__ inline bool packed16_ok(const Scoring &sc)
+{
+    return sc.match <= 1024 && sc.mismatch >= -1024 && sc.gap >= -1024 && sc.x >= 0 &&
+           sc.x + sc.match <= 2046;
+}
+
+template <int L, int C2, class Src>
+__device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, int64_t nw)
+{
+    using namespace p16;
+    constexpr int S = 2 * C2;  // slots per lane
+    constexpr int W = L * S;
+    static_assert(S <= 16 && 32 % L == 0 && C2 % 4 == 0, "packed tile shape");
+    const int lane = threadIdx.x & 31;
+    const int glane = lane % L;
+    const int gbase = lane - glane;
+    const unsigned gm = group_mask<L>(gbase);
+
+    // Per-group task state (uniform within a group).
+    bool active = false, exhausted = false;
+    uint32_t task = 0;
+    const Job *gj = nullptr;
+    Scoring sc{1, -1, -1, 0};
+    int64_t sa0 = 0, sb0 = 0;
+    int dir = 1;
+    int32_t m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
+    int32_t Q = 0;              // frame offset: thr = T + Q
+    int32_t ng = 1;             // |gap|
+    uint32_t ma2 = 0, mi2 = 0;  // packed match / mismatch + 2|gap|
+    bool prev_dead = false;
+    uint32_t E[C2], O[C2];
+#pragma unroll
+    for (int t = 0; t < C2; ++t) { E[t] = kDead2; O[t] = kDead2; }
+    uint32_t Aw = 0, LA = 0, Bw = 0, LB = 0;
+    int la_n = 16, lb_n = 16;  // warp-uniform lookahead counters
+
+    auto retire = [&](bool overflow) {
+        if (glane == 0) src.retire(gj, task, overflow, T, bi, bj);
+        active = false;
+        ng = 0;  // the frame offset stays put while the group waits
+    };
+
+    // Bookkeeping after diagonal d (V holds it).
+    // Group key: value above lane above slot in lane, so one max finds the
+    // lowest window slot among the cells holding the diagonal's maximum.
+    const int32_t lane_bits = (31 - glane) << 4;
+    auto finish = [&](uint32_t (&V)[C2], int32_t lkey, const bool odd) {
+        const int32_t mkey = __reduce_max_sync(gm, (lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
+        const int32_t xm = mkey >> 9;  // best r - thr on the diagonal (-1: none live)
+        if (active && xm > sc.x) {
+            T = T - sc.x + xm;
+            bi = (i0 - glane * S) + (31 - ((mkey >> 4) & 31)) * S + (S - 1 - (mkey & 15));
+            bj = d - bi;
+        }
+        const bool dead = (mkey < 0);
+        bool fin = active && ((dead && prev_dead) || d >= m + n);
+        prev_dead = dead;
+        // Window edges: after an odd diagonal the top slot (high half of the
+        // last lane's last register) may seed a cell above the window, after
+        // an even one the bottom slot (low half of lane 0's register 0).
+        const uint32_t dead16 = (uint32_t)kDead & 0xFFFFu;
+        const uint32_t vedge = odd ? __shfl_sync(FULL, V[C2 - 1], L - 1, L) >> 16
+                                   : __shfl_sync(FULL, V[0], 0, L) & 0xFFFFu;
+        const bool want = active && !fin && vedge != dead16;
+        bool ovf = false;
+        if (__any_sync(FULL, want)) {
+            const uint32_t vopp = odd ? __shfl_sync(FULL, V[0], 0, L) & 0xFFFFu
+                                      : __shfl_sync(FULL, V[C2 - 1], L - 1, L) >> 16;
+            ovf = want && vopp != dead16;
+            const bool sh = want && !ovf;
+            if (odd) {  // shift up: slot s takes slot s+1
+                uint32_t ne = __shfl_down_sync(FULL, E[0], 1, L);
+                uint32_t no = __shfl_down_sync(FULL, O[0], 1, L);
+                if (glane == L - 1) { ne = kDead2; no = kDead2; }
+                if (sh) {
+                    const uint32_t te = prmt(E[0], ne, 0x5432), to = prmt(O[0], no, 0x5432);
+#pragma unroll
+                    for (int t = 0; t < C2 - 1; ++t) { E[t] = E[t + 1]; O[t] = O[t + 1]; }
+                    E[C2 - 1] = te;
+                    O[C2 - 1] = to;
+                    i0 += 1;
+                    j0 -= 1;
+                }
+            } else {    // shift down: slot s takes slot s-1
+                uint32_t pe = __shfl_up_sync(FULL, E[C2 - 1], 1, L);
+                uint32_t po = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
+                if (glane == 0) { pe = kDead2; po = kDead2; }
+                if (sh) {
+                    const uint32_t te = prmt(pe, E[C2 - 1], 0x5432);
+                    const uint32_t to = prmt(po, O[C2 - 1], 0x5432);
+#pragma unroll
+                    for (int t = C2 - 1; t > 0; --t) { E[t] = E[t - 1]; O[t] = O[t - 1]; }
+                    E[0] = te;
+                    O[0] = to;
+                    i0 -= 1;
+                    j0 += 1;
+                }
+            }
+            if (sh) {
+                Aw = fwd16_u(pk, nw, sa0, dir, i0);
+                LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+                Bw = back16_u(pk, nw, sb0, dir, j0);
+                LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+            }
+            fin = fin || ovf;
+        }
+        if (fin) retire(ovf);
+    };
+
+    unsigned turn = 0;
+    for (;;) {
+        if ((++turn & 255u) == 0 && __any_sync(FULL, src.aborted())) break;
+        // ---------------- task switches (top of an odd diagonal) ----------------
+        const bool need = !active && !exhausted;
+        const unsigned needm = __ballot_sync(FULL, need && glane == 0);
+        if (needm) {
+            const int r = src.fetch_warp(needm, lane, gbase, gm, need, task, gj);
+            if (need) {
+                if (r < 0) {
+                    exhausted = true;
+                } else if (r > 0) {
+                    const Ext e = src.open(gj, task, sc);
+                    if (e.ok) {
+                        sa0 = e.A.s0;
+                        sb0 = e.B.s0;
+                        dir = e.A.dir;
+                        m = e.m;
+                        n = e.n;
+                        ng = -sc.gap;
+                        ma2 = pack2(sc.match + 2 * ng);
+                        mi2 = pack2(sc.mismatch + 2 * ng);
+                        // origin (H = 0) at window slot W/2, stored as 0 + x
+#pragma unroll
+                        for (int t = 0; t < C2; ++t) {
+                            const int slo = glane * S + t, shi = slo + C2;
+                            const uint32_t lo = (slo == W / 2) ? (uint32_t)sc.x : (uint32_t)kDead & 0xFFFFu;
+                            const uint32_t hi = (shi == W / 2) ? (uint32_t)sc.x : (uint32_t)kDead & 0xFFFFu;
+                            E[t] = lo | (hi << 16);
+                            O[t] = kDead2;
+                        }
+                        i0 = -(W / 2) + glane * S;
+                        j0 = (W / 2) - glane * S;
+                        Aw = fwd16_u(pk, nw, sa0, dir, i0);
+                        LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+                        Bw = back16_u(pk, nw, sb0, dir, j0);
+                        LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+                        d = 0;
+                        T = 0;
+                        Q = 0;
+                        bi = 0;
+                        bj = 0;
+                        prev_dead = false;
+                        active = true;
+                    }
+                }
+            }
+        }
+        if (__all_sync(FULL, exhausted && !active)) break;
+        if (!__any_sync(FULL, active)) {
+            src.idle();
+            continue;
+        }
+
+        // ---------------- odd diagonal: a-window advances ----------------
+        ++d;
+        ++i0;
+        Q += ng;
+        // keep thr = T + Q below 2*kRebase (see the header comment)
+        const bool rb = active && T + Q >= kRebase;
+        if (__any_sync(FULL, rb)) {
+            if (rb) {
+                const uint32_t mr = pack2(-kRebase);
+#pragma unroll
+                for (int t = 0; t < C2; ++t) {
+                    E[t] = __viaddmax_s16x2(E[t], mr, kDead2);
+                    O[t] = __viaddmax_s16x2(O[t], mr, kDead2);
+                }
+                Q -= kRebase;
+            }
+        }
+        Aw = __funnelshift_r(Aw, LA, 2);
+        LA >>= 2;
+        if (--la_n == 0) {
+            LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+            la_n = 16;
+        }
+        {
+            const uint32_t nthr2 = pack2(-(T + Q));
+            const uint32_t xx = Aw ^ Bw;
+            const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
+            uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
+            if (glane == L - 1) edge = kDead2;
+            const bool nm = active && ((i0 - glane * S + W - 1 > m) || (j0 + glane * S > n));
+            int32_t lkey;
+            if (__any_sync(FULL, nm))
+                lkey = dp16<C2, true, true>(O, E, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            else
+                lkey = dp16<C2, true, false>(O, E, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            finish(O, lkey, true);
+        }
+        // ---------------- even diagonal: b-window advances ----------------
+        ++d;
+        ++j0;
+        Q += ng;
+        Bw = __funnelshift_l(LB, Bw, 2);
+        LB <<= 2;
+        if (--lb_n == 0) {
+            LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+            lb_n = 16;
+        }
+        {
+            const uint32_t nthr2 = pack2(-(T + Q));
+            const uint32_t xx = Aw ^ Bw;
+            const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
+            uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
+            if (glane == 0) edge = kDead2;
+            const bool nm = active && ((i0 - glane * S + W - 1 > m) || (j0 + glane * S > n));
+            int32_t lkey;
+            if (__any_sync(FULL, nm))
+                lkey = dp16<C2, false, true>(E, O, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            else
+                lkey = dp16<C2, false, false>(E, O, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            finish(E, lkey, false);
+        }
+    }
+}
+
+// Batched form of the packed kernel (same task source as lockstep_kernel).
+template <int L, int C2>
+__global__ void __launch_bounds__(256)
+lockstep16_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_ptr,
+                  uint32_t *counter, Spill spill)
+{
+    BatchSrc src{jp, order, *n_tasks_ptr, counter, spill};
+    lockstep16_loop<L, C2>(src, jp->packed, jp->n_words);
+}
+
+}  // namespace xd

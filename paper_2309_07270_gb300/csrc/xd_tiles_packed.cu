@@ -1,0 +1,52 @@
+// Packed 16-bit band tiles (two window slots per register): 4x16 and 8x8
+// (width 64), 8x16 and 16x8 (width 128).
+#include "xd_launch.h"
+#include "xd_lockstep16.cuh"
+
+namespace xd {
+
+template <int L, int C2>
+static cudaError_t packed_impl(int grid, const Job *jp, const uint32_t *order, const uint32_t *n,
+                               uint32_t *ctr, Spill sp, cudaStream_t s)
+{
+    (void)cudaGetLastError();
+    lockstep16_kernel<L, C2><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
+    return cudaGetLastError();
+}
+
+template <int L, int C2>
+static int packed_occupancy_impl()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lockstep16_kernel<L, C2>, 256, 0);
+    return b;
+}
+
+cudaError_t launch_persistent_packed(Tile t, int grid, const Job *jp, const uint32_t *order,
+                                     const uint32_t *n, uint32_t *ctr, Spill sp,
+                                     cudaStream_t s, bool *handled)
+{
+    *handled = true;
+    if (t.packed) {
+        if (t.lanes == 4 && t.c == 16) return packed_impl<4, 8>(grid, jp, order, n, ctr, sp, s);
+        if (t.lanes == 8 && t.c == 8) return packed_impl<8, 4>(grid, jp, order, n, ctr, sp, s);
+        if (t.lanes == 8 && t.c == 16) return packed_impl<8, 8>(grid, jp, order, n, ctr, sp, s);
+        if (t.lanes == 16 && t.c == 8) return packed_impl<16, 4>(grid, jp, order, n, ctr, sp, s);
+    }
+    *handled = false;
+    return cudaSuccess;
+}
+
+int occupancy_packed(Tile t)
+{
+    if (!t.packed) return -1;
+    if (t.lanes == 4 && t.c == 16) return packed_occupancy_impl<4, 8>();
+    if (t.lanes == 8 && t.c == 8) return packed_occupancy_impl<8, 4>();
+    if (t.lanes == 8 && t.c == 16) return packed_occupancy_impl<8, 8>();
+    if (t.lanes == 16 && t.c == 8) return packed_occupancy_impl<16, 4>();
+    return -1;
+}
+
+bool packed_scoring_ok(const Scoring &sc) { return packed16_ok(sc); }
+
+}  // namespace xd

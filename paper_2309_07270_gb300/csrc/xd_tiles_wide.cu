@@ -78,6 +78,9 @@ cudaError_t launch_persistent_mid(Tile, int, const Job *, const uint32_t *, cons
                                   uint32_t *, Spill, cudaStream_t, bool *);
 int occupancy_narrow(Tile);
 int occupancy_mid(Tile);
+cudaError_t launch_persistent_packed(Tile, int, const Job *, const uint32_t *, const uint32_t *,
+                                     uint32_t *, Spill, cudaStream_t, bool *);
+int occupancy_packed(Tile);
 cudaError_t launch_window_plain(const Job *, uint32_t, uint32_t, Spill, cudaStream_t);
 cudaError_t launch_spill_mid(int, const Job *, Spill, Spill, cudaStream_t);
 
@@ -92,6 +95,7 @@ cudaError_t launch_serve(Tile t, int grid, const ServeArgs &a, const uint32_t *p
                          cudaStream_t s)
 {
     bool handled = false;
+    if (t.packed) return cudaErrorInvalidValue;
     cudaError_t e = launch_serve_narrow(t, grid, a, pk, nw, s, &handled);
     if (handled) return e;
     e = launch_serve_mid(t, grid, a, pk, nw, s, &handled);
@@ -101,6 +105,7 @@ cudaError_t launch_serve(Tile t, int grid, const ServeArgs &a, const uint32_t *p
 
 int serve_blocks_per_sm(Tile t)
 {
+    if (t.packed) return -1;
     int b = serve_occupancy_narrow(t);
     if (b < 0) b = serve_occupancy_mid(t);
     return b;
@@ -110,8 +115,8 @@ const Tile kTiles[N_TILES] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4
 
 bool tile_supported(Tile t, bool persistent)
 {
-    if (!persistent) return (t.lanes == 32 && (t.c == 4 || t.c == 16));
-    return occupancy_narrow(t) >= 0 || occupancy_mid(t) >= 0;
+    if (!persistent) return !t.packed && t.lanes == 32 && (t.c == 4 || t.c == 16);
+    return persistent_blocks_per_sm(t) >= 0;
 }
 
 cudaError_t launch_window(Tile t, bool count, const Job *jp, uint32_t task_base,
@@ -127,6 +132,11 @@ cudaError_t launch_persistent(Tile t, int grid, const Job *jp, const uint32_t *o
                               cudaStream_t s)
 {
     bool handled = false;
+    if (t.packed) {
+        cudaError_t e = launch_persistent_packed(t, grid, jp, order, n_tasks, counter, spill, s,
+                                                 &handled);
+        return handled ? e : cudaErrorInvalidValue;
+    }
     cudaError_t e = launch_persistent_narrow(t, grid, jp, order, n_tasks, counter, spill, s,
                                              &handled);
     if (handled) return e;
@@ -137,6 +147,7 @@ cudaError_t launch_persistent(Tile t, int grid, const Job *jp, const uint32_t *o
 
 int persistent_blocks_per_sm(Tile t)
 {
+    if (t.packed) return occupancy_packed(t);
     int b = occupancy_narrow(t);
     if (b < 0) b = occupancy_mid(t);
     return b;

@@ -106,10 +106,16 @@ def test_other_scorings(X, aligners, orc, mode, scores):
     assert_same(run_host(X, aligners[mode], w), oracle_results(orc, w), f"{mode} {scores}")
 
 
-TILES = [(4, 16), (8, 8), (16, 4), (8, 16), (16, 8), (32, 4)]
+P16 = 0x100  # XDROP_TILE_PACKED16
+TILES = [(4, 16), (8, 8), (16, 4), (8, 16), (16, 8), (32, 4),
+         (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16)]
 
 
-@pytest.mark.parametrize("tile", TILES, ids=lambda t: f"{t[0]}x{t[1]}")
+def tile_id(t):
+    return f"{t[0]}x{t[1] & 0xff}" + ("p16" if t[1] & P16 else "")
+
+
+@pytest.mark.parametrize("tile", TILES, ids=tile_id)
 def test_every_first_tile(X, orc, tile):
     """Each first-tier tile (forced, no autotuning) is exact on long,
     ragged and wide-band inputs."""
@@ -121,6 +127,45 @@ def test_every_first_tile(X, orc, tile):
             got = run_host(X, al, w)
             assert al.tile() == tile
             assert_same(got, oracle_results(orc, w), f"tile {tile} {w.name}")
+
+
+PACKED_LIMIT_SCORINGS = [
+    (1024, -1024, -1024, 1022),  # every limit at once: the frame is rebased every diagonal pair
+    (1, -1024, -1, 2045),        # largest x
+    (3, -2, -1024, 100),         # gap-dominated frame growth
+    (1, 0, -1, 50),              # mismatch + 2|gap| > 0
+    (7, -1, -2, 0),              # x = 0
+]
+
+
+@pytest.mark.parametrize("scores", PACKED_LIMIT_SCORINGS, ids=lambda s: "_".join(map(str, s)))
+@pytest.mark.parametrize("tile", [(4, 16 | P16), (8, 8 | P16)], ids=tile_id)
+def test_packed_tiles_at_their_limits(X, orc, tile, scores):
+    """Scorings at the edges of the packed 16-bit range stay exact, on long
+    near-identical pairs (scores and the normalised frame grow fast) and on
+    ragged ones."""
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        al.set_tile(*tile)
+        for w in (W.template_pairs(n_pairs=24, len_lo=1500, len_hi=3000, seed=31),
+                  W.tiny_pairs(n_pairs=150, seed=32, x=9)):
+            w.match, w.mismatch, w.gap, w.x = scores
+            got = run_host(X, al, w)
+            assert al.tile() == tile
+            assert_same(got, oracle_results(orc, w), f"{tile_id(tile)} {scores} {w.name}")
+
+
+@pytest.mark.parametrize("scores", [(1, -1, -1, 2046), (1025, -1, -1, 10), (1, -1025, -1, 10),
+                                    (1, -1, -1025, 10)], ids=lambda s: "_".join(map(str, s)))
+def test_packed_tile_falls_back_outside_its_range(X, orc, scores):
+    """A forced packed tile runs the 32-bit tile of its shape when the
+    scoring does not fit 16 bits, with the same results."""
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        al.set_tile(4, 16 | P16)
+        w = W.template_pairs(n_pairs=12, len_lo=300, len_hi=800, seed=33)
+        w.match, w.mismatch, w.gap, w.x = scores
+        got = run_host(X, al, w)
+        assert al.tile() == (4, 16)
+        assert_same(got, oracle_results(orc, w), f"fallback {scores}")
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -220,3 +265,31 @@ def test_genome_29x_full_size_sampled(X, aligners, orc, genome29, x):
     assert_same(got[idx], want, f"29x x={x}")
     host = run_host(X, al, w.subset(np.arange(0, w.n_pairs, 97)))
     assert np.array_equal(host, got[::97])
+
+
+@pytest.mark.parametrize("x", [50, 100])
+def test_genome_29x_every_pair_every_tile(X, orc, genome29, x):
+    """Every pair of the full 29x workload: each packed tile gives exactly
+    the results of the 32-bit 4x16 tile (whose sample the oracle checks in
+    the test above); any pair where the tiles disagree is also checked
+    against the oracle so that the failure names the wrong one."""
+    w = genome29.with_x(x)
+    dev = X.DeviceInputs.from_workload(w)
+    sc = X.scoring(1, -1, -1, x)
+    tiles = [(4, 16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16)]
+    res = {}
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        for t in tiles:
+            al.set_tile(*t)
+            al.align_device(dev, sc)
+            assert al.tile() == t
+            res[t] = dev.results().view(np.int32).reshape(-1, 7).copy()
+    ref = res[tiles[0]]
+    bad = np.zeros(w.n_pairs, bool)
+    for t in tiles[1:]:
+        bad |= (res[t] != ref).any(axis=1)
+    idx = np.flatnonzero(bad)
+    if idx.size:
+        want = oracle_results(orc, w.subset(idx[:50]), nthreads=16).view(np.int32).reshape(-1, 7)
+        wrong = {tile_id(t): int((res[t][idx[:50]] != want).any(axis=1).sum()) for t in tiles}
+        pytest.fail(f"{idx.size} pairs differ between tiles; wrong of the first 50: {wrong}")

@@ -56,3 +56,13 @@ def test_record_layouts():
     from paper_2309_07270_gb300 import workloads, xdrop
     assert xdrop.PAIR_DTYPE.itemsize == 20 and xdrop.RESULT_DTYPE.itemsize == 28
     assert workloads.PAIR_DTYPE == xdrop.PAIR_DTYPE
+
+
+def test_binding_constants_match_header():
+    """Every #define XDROP_* of the header has the same value in the binding."""
+    from paper_2309_07270_gb300 import xdrop
+    src = open(os.path.join(ROOT, "include", "xdrop.h")).read()
+    defs = re.findall(r"#define\s+(XDROP_\w+)\s+\(?(-?(?:0x[0-9a-fA-F]+|\d+))\)?u?", src)
+    assert len(defs) >= 13
+    for name, val in defs:
+        assert getattr(xdrop, name) == int(val, 0), name
