@@ -238,14 +238,21 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
+def kernel_source_sha():
+    """First 16 hex digits of the sha256 of the band kernels' device sources."""
+    h = hashlib.sha256()
+    for f in ("xd_types.cuh", "xd_device.cuh", "xd_lockstep16.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2309_07270_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(kernel_tag):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_2309_07270_gb300", "csrc", "xd_device.cuh")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     for line in open(path):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kernel_tag and f.get("source_sha") == sha:
@@ -301,8 +308,9 @@ def run_ours(args):
     dev = X.DeviceInputs.from_workload(w, device=dev_name)
     batched = X.Aligner(device=local, mode=X.XDROP_MODE_BATCHED)
     if args.tile:
-        lanes, cpl = (int(v) for v in args.tile.lower().split("x"))
-        batched.set_tile(lanes, cpl)
+        spec = args.tile.lower()
+        lanes, cpl = spec.rstrip("p").split("x")
+        batched.set_tile(int(lanes), int(cpl) | (X.XDROP_TILE_PACKED16 if spec.endswith("p") else 0))
     stream = torch.cuda.ExternalStream(batched.stream(), device=dev_name)
     cells_task = batched.count_cells_device(dev, sc).cpu().numpy()
     cells = int(cells_task.sum())
@@ -397,15 +405,23 @@ def run_ours(args):
     main_mean = statistics.mean(main_ms) if main_ms and min(main_ms) > 0 else None
     achieved = (INT_OPS_PER_CELL * cells_tier0 / (main_mean * 1e-3) / 1e12) if main_mean else None
     tile = batched.tile()
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tint32op/s",
+    packed = bool(tile[1] & X.XDROP_TILE_PACKED16)
+    cpl = tile[1] & 0xff
+    if packed:  # 16-bit cells, two per lane op: the issue limit counts 2 ops per lane
+        kname, op_unit, per_lane = f"lockstep16_kernel<{tile[0]},{cpl // 2}>", "Tint16op/s", 2
+        peak *= 2
+    else:
+        kname, op_unit, per_lane = f"lockstep_kernel<{tile[0]},{cpl}>", "Tint32op/s", 1
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": op_unit,
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_from_profile(f"lockstep_kernel<{tile[0]},{tile[1]}>"),
-            "kernel": f"lockstep_kernel<{tile[0]},{tile[1]}>",
+            "traffic": traffic_from_profile(kname),
+            "kernel": kname,
             "kernel_ms": main_mean,
-            "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes/clk x "
-                          f"{sm_max:.0f} MHz (max SM clock)",
+            "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} lanes/clk x "
+                          f"{per_lane} op per lane x {sm_max:.0f} MHz (max SM clock)",
             "ops_per_cell": INT_OPS_PER_CELL, "cells_in_kernel": cells_tier0,
-            "step_frac": INT_OPS_PER_CELL * cells / (mean_ms * 1e-3) / 1e12 / peak}
+            "step_frac": INT_OPS_PER_CELL * cells / (mean_ms * 1e-3) / 1e12 / peak,
+            "packed16": packed}
 
     serving_runs = None
     if not args.no_serve:
@@ -422,12 +438,13 @@ def run_ours(args):
             cfg["workload"] += f"-first-{w.n_pairs}-pairs"
         cfg.update({"l2": "flushed between steps (256 MiB write outside the timed events)",
                     "form": "batched: binned persistent kernel in a CUDA graph",
-                    "tile0": f"{tile[0]} lanes x {tile[1]} cells", "cells": cells,
+                    "tile0": f"{tile[0]} lanes x {cpl} cells" + (" (16-bit packed)" if packed else ""),
+                    "cells": cells,
                     "parallelism": f"{ws} independent replica(s), no collective"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int32", "data": "synthetic", "config": cfg,
+                "dtype": "int16x2" if packed else "int32", "data": "synthetic", "config": cfg,
                 "pairs_per_s": pairs_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "plain": plain,
                 "batched_over_plain": (value / plain["value"]) if plain else None,

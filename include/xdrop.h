@@ -210,8 +210,10 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
 /* Batched mode: fix the first band tier to `lanes` lanes per extension
  * and `cells` cells per lane (lanes*cells slots per anti-diagonal parity),
  * or pass lanes = 0 to go back to autotuning.  Autotuning (the default)
- * times every first-tier tile on a sample of the first submit with a new
- * scoring and keeps the fastest for that scoring.  Tiles: 4x16, 8x8, 16x4,
+ * times the first-tier tiles on a sample of the first submit with a new
+ * scoring (the packed tiles on a third of it when the scoring fits them,
+ * else the 32-bit tiles on an eighth) and keeps the fastest for that
+ * scoring.  Tiles: 4x16, 8x8, 16x4,
  * 8x16, 16x8, 32x4, and packed (cells | XDROP_TILE_PACKED16) 4x16, 8x8,
  * 8x16, 16x8.  Returns XDROP_EINVAL for another shape.  Serving mode uses
  * the 32-bit tile of a packed shape. */

@@ -261,8 +261,15 @@ int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out);
 int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
 {
     cudaStream_t s = c->stream;
+    // Scorings that fit 16 bits choose among the packed tiles only (each is
+    // faster than the 32-bit tile of its shape), on a third of the job so
+    // the end of the sample, where few extensions are left, does not decide
+    // between tiles of different concurrency; other scorings time the
+    // 32-bit tiles on an eighth.
+    const bool packed = packed_scoring_ok(job.sc);
     Job js = job;
-    js.n_pairs = std::min<uint64_t>(job.n_pairs, std::max<uint64_t>(4096, job.n_pairs / 8));
+    js.n_pairs = std::min<uint64_t>(job.n_pairs,
+                                    std::max<uint64_t>(4096, job.n_pairs / (packed ? 3 : 8)));
     CK(cudaStreamSynchronize(s));
     *tk->h_job = js;
     CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
@@ -271,8 +278,9 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     *best = Tile{0, 0};
-    std::vector<Tile> cands(std::begin(kTuneTiles), std::end(kTuneTiles));
-    if (packed_scoring_ok(job.sc)) cands.insert(cands.end(), std::begin(kPackedTiles), std::end(kPackedTiles));
+    std::vector<Tile> cands;
+    if (packed) cands.assign(std::begin(kPackedTiles), std::end(kPackedTiles));
+    else cands.assign(std::begin(kTuneTiles), std::end(kTuneTiles));
     for (const Tile &t : cands) {
         const int bps = persistent_blocks_per_sm(t);
         if (bps <= 0) continue;

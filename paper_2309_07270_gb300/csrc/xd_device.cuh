@@ -549,6 +549,7 @@ __device__ __forceinline__ void store_result_cg(const Job &J, uint32_t task, int
 // Task source of the batched form: positions of a longest-first order
 // array pulled from a global counter; overflowing tasks go to a spill list.
 struct BatchSrc {
+    static constexpr bool kCanAbort = false;  // teardown may stop the loop
     const Job *jp;
     const uint32_t *order;
     uint32_t n_tasks;
@@ -843,6 +844,7 @@ __device__ __forceinline__ void serve_list_wide(const ServeArgs &a, const Job *g
 constexpr unsigned long long kSpillBacklog = 64;  // ring warps switch tiers above this
 
 struct RingSrc {
+    static constexpr bool kCanAbort = true;  // teardown may stop the loop
     ServeArgs a;
     unsigned long long idle_since;
     int backoff;   // loop turns before the next poll (leader)
@@ -962,6 +964,7 @@ struct RingSrc {
 };
 
 struct SpillSrc {
+    static constexpr bool kCanAbort = true;  // teardown may stop the loop
     ServeArgs a;
     int backoff;
     int level;

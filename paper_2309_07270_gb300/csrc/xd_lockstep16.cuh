@@ -33,6 +33,10 @@
 // among equal values, the lowest window slot (lane first, then slot), i.e.
 // the first cell in order of increasing i on the diagonal.
 #pragma once
+#include <stdint.h>
+
+#include <type_traits>
+
 #include "xd_device.cuh"
 
 namespace xd {
@@ -156,12 +160,15 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     int32_t Q = 0;              // frame offset: thr = T + Q
     int32_t ng = 1;             // |gap|
     uint32_t ma2 = 0, mi2 = 0;  // packed match / mismatch + 2|gap|
-    bool prev_dead = false;
+    bool prev_dead = false, fin = false, want = false;
     uint32_t E[C2], O[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) { E[t] = kDead2; O[t] = kDead2; }
     uint32_t Aw = 0, LA = 0, Bw = 0, LB = 0;
     int la_n = 16, lb_n = 16;  // warp-uniform lookahead counters
+    int32_t budget = 0;        // warp-uniform: half-steps known to stay inside every rectangle
+    const int32_t lane_bits = (31 - glane) << 4;
+    const uint32_t dead16 = (uint32_t)kDead & 0xFFFFu;
 
     auto retire = [&](bool overflow) {
         if (glane == 0) src.retire(gj, task, overflow, T, bi, bj);
@@ -169,32 +176,84 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         ng = 0;  // the frame offset stays put while the group waits
     };
 
-    // Bookkeeping after diagonal d (V holds it).
-    // Group key: value above lane above slot in lane, so one max finds the
-    // lowest window slot among the cells holding the diagonal's maximum.
-    const int32_t lane_bits = (31 - glane) << 4;
-    auto finish = [&](uint32_t (&V)[C2], int32_t lkey, const bool odd) {
+    // Half-steps until a cell of this group's window can leave the
+    // rectangle: each half-step moves the top slot's i or the bottom
+    // slot's j up by one (window shifts recompute it).
+    auto refresh_budget = [&]() {
+        const int32_t mg = min(m - (i0 - glane * S + W - 1), n - (j0 + glane * S));
+        budget = __reduce_min_sync(FULL, active ? mg : INT32_MAX);
+    };
+
+    // One anti-diagonal.  Returns the warp-wide "something to do" vote:
+    // a window edge went live, a task ended, a lookahead word ran out, the
+    // frame needs a rebase, the masking-free budget ran low, or a group
+    // waits for a task.  Everything else is straight-line code.
+    auto half = [&](auto odd_tag, auto masked_tag) -> bool {
+        constexpr bool ODD = decltype(odd_tag)::value;
+        constexpr bool MASKED = decltype(masked_tag)::value;
+        ++d;
+        Q += ng;
+        --budget;
+        if (ODD) {
+            ++i0;
+            Aw = __funnelshift_r(Aw, LA, 2);
+            LA >>= 2;
+            --la_n;
+        } else {
+            ++j0;
+            Bw = __funnelshift_l(LB, Bw, 2);
+            LB <<= 2;
+            --lb_n;
+        }
+        const uint32_t nthr2 = pack2(-(T + Q));
+        const uint32_t xx = Aw ^ Bw;
+        const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
+        int32_t lkey;
+        uint32_t vedge;
+        if (ODD) {
+            uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
+            if (glane == L - 1) edge = kDead2;
+            lkey = dp16<C2, true, MASKED>(O, E, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            vedge = __shfl_sync(FULL, O[C2 - 1], L - 1, L) >> 16;
+        } else {
+            uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
+            if (glane == 0) edge = kDead2;
+            lkey = dp16<C2, false, MASKED>(E, O, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            vedge = __shfl_sync(FULL, E[0], 0, L) & 0xFFFFu;
+        }
+        // Group key: value above lane above slot in lane, so one max finds
+        // the lowest window slot among the cells holding the maximum.
         const int32_t mkey = __reduce_max_sync(gm, (lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
         const int32_t xm = mkey >> 9;  // best r - thr on the diagonal (-1: none live)
-        if (active && xm > sc.x) {
-            T = T - sc.x + xm;
-            bi = (i0 - glane * S) + (31 - ((mkey >> 4) & 31)) * S + (S - 1 - (mkey & 15));
-            bj = d - bi;
-        }
+        const int32_t nbi = (i0 - glane * S) + (31 - ((mkey >> 4) & 31)) * S + (S - 1 - (mkey & 15));
+        const bool up = active && xm > sc.x;
+        T = up ? T - sc.x + xm : T;
+        bi = up ? nbi : bi;
+        bj = up ? d - nbi : bj;
         const bool dead = (mkey < 0);
-        bool fin = active && ((dead && prev_dead) || d >= m + n);
+        fin = active && ((dead && prev_dead) || d >= m + n);
         prev_dead = dead;
-        // Window edges: after an odd diagonal the top slot (high half of the
-        // last lane's last register) may seed a cell above the window, after
-        // an even one the bottom slot (low half of lane 0's register 0).
-        const uint32_t dead16 = (uint32_t)kDead & 0xFFFFu;
-        const uint32_t vedge = odd ? __shfl_sync(FULL, V[C2 - 1], L - 1, L) >> 16
-                                   : __shfl_sync(FULL, V[0], 0, L) & 0xFFFFu;
-        const bool want = active && !fin && vedge != dead16;
+        want = active && !fin && vedge != dead16;
+        bool ev = want || fin || (ODD ? la_n == 0 : lb_n == 0);
+        if (!ODD) {
+            ev = ev || (active && T + Q + ng >= kRebase) || !active;
+            if (!MASKED) ev = ev || budget < 2;
+        }
+        return __any_sync(FULL, ev);
+    };
+
+    // The rare work behind an event.  After an even diagonal, returns true
+    // when the loop must go back to the task switch (a group waits for a
+    // task, no group is left running, or the masking-free budget no longer
+    // covers a diagonal pair).
+    auto handle = [&](const bool odd, const bool masked) -> bool {
         bool ovf = false;
         if (__any_sync(FULL, want)) {
-            const uint32_t vopp = odd ? __shfl_sync(FULL, V[0], 0, L) & 0xFFFFu
-                                      : __shfl_sync(FULL, V[C2 - 1], L - 1, L) >> 16;
+            // After an odd diagonal the top slot may seed a cell above the
+            // window, after an even one the bottom slot one below it; with
+            // the opposite edge live too the task goes to a wider tier.
+            const uint32_t vopp = odd ? __shfl_sync(FULL, O[0], 0, L) & 0xFFFFu
+                                      : __shfl_sync(FULL, E[C2 - 1], L - 1, L) >> 16;
             ovf = want && vopp != dead16;
             const bool sh = want && !ovf;
             if (odd) {  // shift up: slot s takes slot s+1
@@ -234,11 +293,43 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             fin = fin || ovf;
         }
         if (fin) retire(ovf);
+        if (la_n == 0) {
+            LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+            la_n = 16;
+        }
+        if (lb_n == 0) {
+            LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+            lb_n = 16;
+        }
+        if (odd) {
+            if (!masked) refresh_budget();
+            return false;
+        }
+        // Keep thr = T + Q of the next diagonal below 2 * kRebase (see the
+        // header comment): rebase once it would reach kRebase.
+        const bool rb = active && T + Q + ng >= kRebase;
+        if (rb) {
+            const uint32_t mr = pack2(-kRebase);
+#pragma unroll
+            for (int t = 0; t < C2; ++t) {
+                E[t] = __viaddmax_s16x2(E[t], mr, kDead2);
+                O[t] = __viaddmax_s16x2(O[t], mr, kDead2);
+            }
+            Q -= kRebase;
+        }
+        if (!masked) refresh_budget();
+        return __any_sync(FULL, !active && !exhausted) || !__any_sync(FULL, active) ||
+               (!masked && budget < 2);
     };
 
+    using T0 = std::integral_constant<bool, false>;
+    using T1 = std::integral_constant<bool, true>;
     unsigned turn = 0;
     for (;;) {
-        if ((++turn & 255u) == 0 && __any_sync(FULL, src.aborted())) break;
+        // A serving kernel can be told to leave at once (teardown).
+        if constexpr (Src::kCanAbort) {
+            if ((++turn & 15u) == 0 && __any_sync(FULL, src.aborted())) break;
+        }
         // ---------------- task switches (top of an odd diagonal) ----------------
         const bool need = !active && !exhausted;
         const unsigned needm = __ballot_sync(FULL, need && glane == 0);
@@ -262,8 +353,8 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
 #pragma unroll
                         for (int t = 0; t < C2; ++t) {
                             const int slo = glane * S + t, shi = slo + C2;
-                            const uint32_t lo = (slo == W / 2) ? (uint32_t)sc.x : (uint32_t)kDead & 0xFFFFu;
-                            const uint32_t hi = (shi == W / 2) ? (uint32_t)sc.x : (uint32_t)kDead & 0xFFFFu;
+                            const uint32_t lo = (slo == W / 2) ? (uint32_t)sc.x : dead16;
+                            const uint32_t hi = (shi == W / 2) ? (uint32_t)sc.x : dead16;
                             E[t] = lo | (hi << 16);
                             O[t] = kDead2;
                         }
@@ -289,67 +380,17 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             src.idle();
             continue;
         }
-
-        // ---------------- odd diagonal: a-window advances ----------------
-        ++d;
-        ++i0;
-        Q += ng;
-        // keep thr = T + Q below 2*kRebase (see the header comment)
-        const bool rb = active && T + Q >= kRebase;
-        if (__any_sync(FULL, rb)) {
-            if (rb) {
-                const uint32_t mr = pack2(-kRebase);
-#pragma unroll
-                for (int t = 0; t < C2; ++t) {
-                    E[t] = __viaddmax_s16x2(E[t], mr, kDead2);
-                    O[t] = __viaddmax_s16x2(O[t], mr, kDead2);
-                }
-                Q -= kRebase;
+        refresh_budget();
+        if (budget >= 2) {
+            for (;;) {  // no cell of any window can leave its rectangle
+                if (half(T1{}, T0{})) handle(true, false);
+                if (half(T0{}, T0{}) && handle(false, false)) break;
             }
-        }
-        Aw = __funnelshift_r(Aw, LA, 2);
-        LA >>= 2;
-        if (--la_n == 0) {
-            LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
-            la_n = 16;
-        }
-        {
-            const uint32_t nthr2 = pack2(-(T + Q));
-            const uint32_t xx = Aw ^ Bw;
-            const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
-            uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
-            if (glane == L - 1) edge = kDead2;
-            const bool nm = active && ((i0 - glane * S + W - 1 > m) || (j0 + glane * S > n));
-            int32_t lkey;
-            if (__any_sync(FULL, nm))
-                lkey = dp16<C2, true, true>(O, E, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
-            else
-                lkey = dp16<C2, true, false>(O, E, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
-            finish(O, lkey, true);
-        }
-        // ---------------- even diagonal: b-window advances ----------------
-        ++d;
-        ++j0;
-        Q += ng;
-        Bw = __funnelshift_l(LB, Bw, 2);
-        LB <<= 2;
-        if (--lb_n == 0) {
-            LB = back16_u(pk, nw, sb0, dir, j0 + 16);
-            lb_n = 16;
-        }
-        {
-            const uint32_t nthr2 = pack2(-(T + Q));
-            const uint32_t xx = Aw ^ Bw;
-            const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
-            uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
-            if (glane == 0) edge = kDead2;
-            const bool nm = active && ((i0 - glane * S + W - 1 > m) || (j0 + glane * S > n));
-            int32_t lkey;
-            if (__any_sync(FULL, nm))
-                lkey = dp16<C2, false, true>(E, O, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
-            else
-                lkey = dp16<C2, false, false>(E, O, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
-            finish(E, lkey, false);
+        } else {
+            for (;;) {
+                if (half(T1{}, T1{})) handle(true, true);
+                if (half(T0{}, T1{}) && handle(false, true)) break;
+            }
         }
     }
 }
