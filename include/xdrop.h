@@ -202,9 +202,9 @@ void *xdrop_stream(xdrop_ctx *c);
 int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
 
 /* Packed tiles: 16-bit cells, two per 32-bit register, for scorings with
- * match <= 1024, mismatch >= -1024, gap >= -1024 and x + match <= 2046
- * (results identical to the 32-bit tiles; other scorings run the 32-bit
- * tile of the same shape).  Set in `cells` of xdrop_set_tile. */
+ * match - gap <= 128, mismatch >= -128 and x + match <= 1536 (results
+ * identical to the 32-bit tiles; other scorings run the 32-bit tile of
+ * the same shape).  Set in `cells` of xdrop_set_tile. */
 #define XDROP_TILE_PACKED16 0x100
 
 /* Batched mode: fix the first band tier to `lanes` lanes per extension

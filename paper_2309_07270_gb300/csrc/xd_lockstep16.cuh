@@ -3,16 +3,25 @@
 // Same extension, same reading of the X-drop recurrence and the same
 // results as lockstep_loop (xd_device.cuh); only the arithmetic changes.
 // It is exact whenever the scoring passes packed16_ok():
-//   match <= 1024, mismatch >= -1024, gap >= -1024, x + match <= 2046.
+//   match - gap <= 128, mismatch >= -128, x + match <= 1536.
 //
-// Normalised scores.  A cell on anti-diagonal d is stored as
-//   r = H + x + d*|gap| - B
-// (B = the multiples of kRebase taken off so far).  Then the two gap
-// predecessors enter unchanged and the diagonal one with s + 2|gap|:
+// Normalised scores.  A cell on anti-diagonal d holds
+//   r = H + x + d*|gap| - B          (B: multiples of kRebase taken off)
+// stored as 16*r.  Then the two gap predecessors enter unchanged and the
+// diagonal one with s + 2|gap|:
 //   r(d) = max(r_diag(d-2) + s + 2|gap|,  r_up(d-1),  r_left(d-1)),
 // one DPX max and one DPX add-max per register (two cells).  The
 // threshold of diagonal d (T of d-1 minus x) becomes thr = T + d*|gap| - B,
-// a cell is live iff r >= thr, and x_rel = r - thr <= x + match < 2047.
+// a cell is live iff r >= thr, and r - thr <= x + match.
+//
+// Key.  One more DPX add-max gives each slot's key
+//   16*(r - thr) + (S-1-slot), floored at -16,
+// which is negative exactly for the cells the X-drop test prunes (their
+// stored value becomes kDead by the key's sign mask) and, for live cells,
+// orders by value and then by lowest slot.  The lane's best key becomes
+// (key >> 4) * 512 + (31 - lane) * 16 + (key & 15) in 32 bits, so one
+// group max gives the largest value and, among equal values, the lowest
+// window slot: the first cell in order of increasing i on the diagonal.
 //
 // Layout.  Lane g of a group of L lanes holds the window slots g*S .. g*S+S-1
 // (S = 2*C2 slots).  Register t holds slot t in its low half and slot t+C2
@@ -20,18 +29,14 @@
 // register t sits in register t+1 (t-1) at the same half; only the end
 // registers need a byte permute and one shuffle per diagonal.
 //
-// Ranges (no 16-bit wrap anywhere): dead slots hold kDead = -12288; thr
-// stays in [0, 8192) because every odd diagonal subtracts kRebase from the
-// frame once thr reaches kRebase and thr grows by at most 2*(match+|gap|)
-// <= 4096 per diagonal pair; live values stay below 8192 + 2047; a value
-// built from dead predecessors stays below kDead + match + 2|gap| < 0; the
-// relative value r - thr stays above -21504.
-//
-// Best cell.  The key of a slot is max(r - thr, -1) * 16 + (S-1-slot) in
-// 16 bits; the lane's best key becomes value * 512 + (31 - lane) * 16 +
-// (S-1-slot) in 32 bits, so one group max gives the largest value and,
-// among equal values, the lowest window slot (lane first, then slot), i.e.
-// the first cell in order of increasing i on the diagonal.
+// Ranges, in units of r (no 16-bit wrap anywhere, all values times 16 below
+// 2^15): the frame is rebased by kRebase = 256 once thr would reach it, and
+// thr grows by at most 2*(match+|gap|) <= 256 per diagonal pair, so thr
+// stays in [0, 512); live values stay at or below 511 + x + match <= 2047
+// and at or above -256 right after a rebase; dead slots hold -512, and a
+// value built from dead predecessors stays at or below -512 + match +
+// 2|gap| <= -256 < thr; the lowest value formed is above -640 and the
+// lowest key sum above -18432.
 #pragma once
 #include <stdint.h>
 
@@ -43,9 +48,10 @@ namespace xd {
 
 namespace p16 {
 
-constexpr int32_t kDead = -12288;
-constexpr uint32_t kDead2 = 0xD000D000u;  // kDead in both halves
-constexpr int32_t kRebase = 4096;
+constexpr int32_t kScale = 16;            // stored value = 16 * r
+constexpr int32_t kDead = -512 * kScale;  // stored value of a pruned slot
+constexpr uint32_t kDead2 = 0xE000E000u;  // kDead in both halves
+constexpr int32_t kRebase = 256;          // frame step, in units of r
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 {
@@ -118,10 +124,12 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
             if (i0 + t > m || j0 - t > n) r = (r & 0xFFFF0000u) | (kDead2 & 0xFFFFu);
             if (i0 + t + C2 > m || j0 - t - C2 > n) r = (r & 0xFFFFu) | (kDead2 & 0xFFFF0000u);
         }
-        const uint32_t x = __viaddmax_s16x2(r, nthr2, 0xFFFFFFFFu);  // max(r - thr, -1)
-        const uint32_t pm = prmt(x, x, 0xBB99);                      // 0xFFFF where dead
+        // 16*(r - thr) + (S-1-slot), floored at -16: negative iff pruned
+        const uint32_t kc = __viaddmax_s16x2(idx2<C2>(t), nthr2, 0x80008000u);
+        const uint32_t k = __viaddmax_s16x2(r, kc, 0xFFF0FFF0u);
+        const uint32_t pm = prmt(k, k, 0xBB99);  // 0xFFFF where pruned
         V[t] = (r & ~pm) | (kDead2 & pm);
-        key[t] = ((x << 4) & 0xFFF0FFF0u) | idx2<C2>(t);
+        key[t] = k;
     }
     const uint32_t kk = tree_max2<C2>(key);
     const int32_t hi = (int32_t)kk >> 16;
@@ -133,8 +141,8 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
 
 __host__ __device__ inline bool packed16_ok(const Scoring &sc)
 {
-    return sc.match <= 1024 && sc.mismatch >= -1024 && sc.gap >= -1024 && sc.x >= 0 &&
-           sc.x + sc.match <= 2046;
+    return sc.match - sc.gap <= 128 && sc.mismatch >= -128 && sc.x >= 0 &&
+           sc.x + sc.match <= 1536;
 }
 
 template <int L, int C2, class Src>
@@ -205,7 +213,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             LB <<= 2;
             --lb_n;
         }
-        const uint32_t nthr2 = pack2(-(T + Q));
+        const uint32_t nthr2 = pack2(-kScale * (T + Q));
         const uint32_t xx = Aw ^ Bw;
         const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
         int32_t lkey;
@@ -309,7 +317,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         // header comment): rebase once it would reach kRebase.
         const bool rb = active && T + Q + ng >= kRebase;
         if (rb) {
-            const uint32_t mr = pack2(-kRebase);
+            const uint32_t mr = pack2(-kScale * kRebase);
 #pragma unroll
             for (int t = 0; t < C2; ++t) {
                 E[t] = __viaddmax_s16x2(E[t], mr, kDead2);
@@ -347,14 +355,14 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         m = e.m;
                         n = e.n;
                         ng = -sc.gap;
-                        ma2 = pack2(sc.match + 2 * ng);
-                        mi2 = pack2(sc.mismatch + 2 * ng);
-                        // origin (H = 0) at window slot W/2, stored as 0 + x
+                        ma2 = pack2(kScale * (sc.match + 2 * ng));
+                        mi2 = pack2(kScale * (sc.mismatch + 2 * ng));
+                        // origin (H = 0) at window slot W/2, stored as 16 * (0 + x)
 #pragma unroll
                         for (int t = 0; t < C2; ++t) {
                             const int slo = glane * S + t, shi = slo + C2;
-                            const uint32_t lo = (slo == W / 2) ? (uint32_t)sc.x : dead16;
-                            const uint32_t hi = (shi == W / 2) ? (uint32_t)sc.x : dead16;
+                            const uint32_t lo = (slo == W / 2) ? (uint32_t)(kScale * sc.x) : dead16;
+                            const uint32_t hi = (shi == W / 2) ? (uint32_t)(kScale * sc.x) : dead16;
                             E[t] = lo | (hi << 16);
                             O[t] = kDead2;
                         }
