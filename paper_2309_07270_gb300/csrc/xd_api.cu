@@ -804,8 +804,9 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
         rr.read_len = (const uint32_t *)c->r_len.p;
         rr.n_reads = n_reads;
         std::string err;
-        Tile t = c->forced.lanes ? c->forced : Tile{4, 16};
-        t.packed = false;  // the serving kernel has 32-bit tiles only
+        // Packed 4x16 unless a tile was forced; requests whose scoring does
+        // not fit 16 bits run on the serving kernel's 32-bit second tier.
+        const Tile t = c->forced.lanes ? c->forced : Tile{4, 16, true};
         c->srv = xd::server_create(c->device, c->sm_count, c->budget, t, rr, c->h_len.data(),
                                    (int32_t *)c->wide.p, c->wide_per_cta, c->wide_grid, err);
         if (!c->srv) return fail(XDROP_ECUDA, "%s", err.c_str());

@@ -326,17 +326,19 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             Q -= kRebase;
         }
         if (!masked) refresh_budget();
+        if constexpr (Src::kCanAbort) {
+            if (__any_sync(FULL, src.aborted())) return true;
+        }
         return __any_sync(FULL, !active && !exhausted) || !__any_sync(FULL, active) ||
                (!masked && budget < 2);
     };
 
     using T0 = std::integral_constant<bool, false>;
     using T1 = std::integral_constant<bool, true>;
-    unsigned turn = 0;
     for (;;) {
         // A serving kernel can be told to leave at once (teardown).
         if constexpr (Src::kCanAbort) {
-            if ((++turn & 15u) == 0 && __any_sync(FULL, src.aborted())) break;
+            if (__any_sync(FULL, src.aborted())) break;
         }
         // ---------------- task switches (top of an odd diagonal) ----------------
         const bool need = !active && !exhausted;
@@ -348,7 +350,11 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                     exhausted = true;
                 } else if (r > 0) {
                     const Ext e = src.open(gj, task, sc);
-                    if (e.ok) {
+                    if (e.ok && !packed16_ok(sc)) {
+                        // A scoring 16-bit cells cannot hold exactly (a serving
+                        // request's own): hand the task to the next, 32-bit tier.
+                        if (glane == 0) src.retire(gj, task, true, 0, 0, 0);
+                    } else if (e.ok) {
                         sa0 = e.A.s0;
                         sb0 = e.B.s0;
                         dir = e.A.dir;
@@ -411,6 +417,31 @@ lockstep16_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_
 {
     BatchSrc src{jp, order, *n_tasks_ptr, counter, spill};
     lockstep16_loop<L, C2>(src, jp->packed, jp->n_words);
+}
+
+// Serving form: ring warps run the packed tile, the spill warps (one warp
+// in kSpillWarpEvery, plus ring warps that help when the second-tier
+// backlog grows) the 32-bit tile L2 x C2, which also takes every task
+// whose scoring does not fit 16 bits.  Same protocol as serve_kernel.
+template <int L1, int C2a, int L2, int C2>
+__global__ void __launch_bounds__(256, (L1 * 2 * C2a <= 64) ? 3 : 2)
+serve16_kernel(ServeArgs a, const uint32_t *pk, int64_t nw)
+{
+    const unsigned warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp_global % kSpillWarpEvery == kSpillWarpEvery - 1) {
+        SpillSrc src{a, 0, 0, false, false};
+        lockstep_loop<L2, C2>(src, pk, nw);
+        return;
+    }
+    for (;;) {
+        RingSrc src{a, 0ull, 0, 0, false};
+        lockstep16_loop<L1, C2a>(src, pk, nw);
+        if (__any_sync(FULL, src.leaving || src.aborted())) break;
+        SpillSrc help{a, 0, 0, true, false};
+        lockstep_loop<L2, C2>(help, pk, nw);
+        if (__any_sync(FULL, help.failed || help.aborted())) break;
+    }
+    if ((threadIdx.x & 31) == 0) atomicSub(&a.ctl->ring_alive, 1u);
 }
 
 }  // namespace xd

@@ -49,4 +49,47 @@ int occupancy_packed(Tile t)
 
 bool packed_scoring_ok(const Scoring &sc) { return packed16_ok(sc); }
 
+template <int L1, int C2a, int L2, int C2>
+static cudaError_t serve16_impl(int grid, const ServeArgs &a, const uint32_t *pk, int64_t nw,
+                                cudaStream_t s)
+{
+    (void)cudaGetLastError();
+    serve16_kernel<L1, C2a, L2, C2><<<grid, 256, 0, s>>>(a, pk, nw);
+    return cudaGetLastError();
+}
+
+template <int L1, int C2a, int L2, int C2>
+static int serve16_occupancy_impl()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, serve16_kernel<L1, C2a, L2, C2>, 256, 0);
+    return b;
+}
+
+// Second tier as for the 32-bit tiles: 16x8 after a 64-slot first tier,
+// 32x16 after a 128-slot one.
+cudaError_t launch_serve_packed(Tile t, int grid, const ServeArgs &a, const uint32_t *pk,
+                                int64_t nw, cudaStream_t s, bool *handled)
+{
+    *handled = true;
+    if (t.packed) {
+        if (t.lanes == 4 && t.c == 16) return serve16_impl<4, 8, 16, 8>(grid, a, pk, nw, s);
+        if (t.lanes == 8 && t.c == 8) return serve16_impl<8, 4, 16, 8>(grid, a, pk, nw, s);
+        if (t.lanes == 8 && t.c == 16) return serve16_impl<8, 8, 32, 16>(grid, a, pk, nw, s);
+        if (t.lanes == 16 && t.c == 8) return serve16_impl<16, 4, 32, 16>(grid, a, pk, nw, s);
+    }
+    *handled = false;
+    return cudaSuccess;
+}
+
+int serve_occupancy_packed(Tile t)
+{
+    if (!t.packed) return -1;
+    if (t.lanes == 4 && t.c == 16) return serve16_occupancy_impl<4, 8, 16, 8>();
+    if (t.lanes == 8 && t.c == 8) return serve16_occupancy_impl<8, 4, 16, 8>();
+    if (t.lanes == 8 && t.c == 16) return serve16_occupancy_impl<8, 8, 32, 16>();
+    if (t.lanes == 16 && t.c == 8) return serve16_occupancy_impl<16, 4, 32, 16>();
+    return -1;
+}
+
 }  // namespace xd

@@ -81,6 +81,9 @@ int occupancy_mid(Tile);
 cudaError_t launch_persistent_packed(Tile, int, const Job *, const uint32_t *, const uint32_t *,
                                      uint32_t *, Spill, cudaStream_t, bool *);
 int occupancy_packed(Tile);
+cudaError_t launch_serve_packed(Tile, int, const ServeArgs &, const uint32_t *, int64_t,
+                                cudaStream_t, bool *);
+int serve_occupancy_packed(Tile);
 cudaError_t launch_window_plain(const Job *, uint32_t, uint32_t, Spill, cudaStream_t);
 cudaError_t launch_spill_mid(int, const Job *, Spill, Spill, cudaStream_t);
 
@@ -95,7 +98,10 @@ cudaError_t launch_serve(Tile t, int grid, const ServeArgs &a, const uint32_t *p
                          cudaStream_t s)
 {
     bool handled = false;
-    if (t.packed) return cudaErrorInvalidValue;
+    if (t.packed) {
+        cudaError_t e = launch_serve_packed(t, grid, a, pk, nw, s, &handled);
+        return handled ? e : cudaErrorInvalidValue;
+    }
     cudaError_t e = launch_serve_narrow(t, grid, a, pk, nw, s, &handled);
     if (handled) return e;
     e = launch_serve_mid(t, grid, a, pk, nw, s, &handled);
@@ -105,7 +111,7 @@ cudaError_t launch_serve(Tile t, int grid, const ServeArgs &a, const uint32_t *p
 
 int serve_blocks_per_sm(Tile t)
 {
-    if (t.packed) return -1;
+    if (t.packed) return serve_occupancy_packed(t);
     int b = serve_occupancy_narrow(t);
     if (b < 0) b = serve_occupancy_mid(t);
     return b;

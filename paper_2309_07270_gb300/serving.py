@@ -103,6 +103,7 @@ class Result:
         self.wall_s = 0.0
         self.errors = []
         self.outputs = {}
+        self.serve_stats = None  # device-loop: the serving loop's counters
 
     def summary(self):
         return {"policy": self.policy, "rho": self.rho,
@@ -112,7 +113,8 @@ class Result:
                 "p50_ms": _percentile(self.latencies, 50) * 1e3 if self.latencies else None,
                 "p99_ms": _percentile(self.latencies, 99) * 1e3 if self.latencies else None,
                 "mean_ms": statistics.mean(self.latencies) * 1e3 if self.latencies else None,
-                "errors": len(self.errors)}
+                "errors": len(self.errors),
+                "serve_stats": self.serve_stats}
 
 
 def run_policy(policy, pool, schedule, sc, device=0, budget=0, tile=None, keep_outputs=False,
@@ -224,6 +226,8 @@ def run_policy(policy, pool, schedule, sc, device=0, budget=0, tile=None, keep_o
     for w in waiters:
         w.join()
     res.wall_s = time.perf_counter() - t0
+    if policy == "device-loop":
+        res.serve_stats = X.xdrop_get_serve_stats(ctxs[0])
     for c in {id(c): c for c in ctxs}.values():
         X.xdrop_free(c)
     if ring is not None:

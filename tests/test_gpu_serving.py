@@ -178,3 +178,47 @@ def test_submit_pairs_outside_serving(X, orc, pool):
     want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
                            1, -1, -1, 50, nthreads=8)
     assert np.array_equal(out.view(np.int32), want.view(np.int32))
+
+
+def test_mixed_scorings_packed_and_not(X, orc, pool):
+    """Producers with different scorings share the serving kernel: one
+    scoring fits the packed first tier, the other (mismatch -200) does
+    not and runs on the 32-bit second tier.  Every request equals the
+    oracle for its own scoring."""
+    reqs = requests_for(pool, n_producers=8, per_producer=2, lo=40, hi=200, seed=700)
+    scs = [(1, -1, -1, 50), (2, -200, -3, 60)]
+    ctx = serve_ctx(X, pool)
+    outs, errors = [None] * len(reqs), []
+
+    def producer(items):
+        try:
+            tickets = []
+            for i in items:
+                p = reqs[i][0]
+                out = np.zeros(len(reqs[i][1]), X.RESULT_DTYPE)
+                outs[i] = out
+                tickets.append(X.xdrop_submit_pairs(ctx, pool.pairs[reqs[i][1]],
+                                                    X.scoring(*scs[p % 2]), out))
+            for t in tickets:
+                sync(X, ctx, t)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    by_prod = {}
+    for i, (p, _) in enumerate(reqs):
+        by_prod.setdefault(p, []).append(i)
+    try:
+        th = [threading.Thread(target=producer, args=(items,)) for items in by_prod.values()]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(timeout=300)
+        st = X.xdrop_get_serve_stats(ctx)
+    finally:
+        X.xdrop_free(ctx)
+    assert not errors, errors
+    assert st["spill_taken"] > 0  # the second tier ran the unpacked scoring
+    for i, (p, idx) in enumerate(reqs):
+        want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
+                               *scs[p % 2], nthreads=8)
+        assert np.array_equal(outs[i].view(np.int32), want.view(np.int32)), (i, scs[p % 2])
