@@ -166,6 +166,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     int dir = 1;
     int32_t m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
     int32_t Q = 0;              // frame offset: thr = T + Q
+    int32_t bkey = 0, bbase = 0, bd = 0;  // best cell: group key, window base i, diagonal
     int32_t ng = 1;             // |gap|
     uint32_t ma2 = 0, mi2 = 0;  // packed match / mismatch + 2|gap|
     bool prev_dead = false, fin = false, want = false;
@@ -179,6 +180,10 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     const uint32_t dead16 = (uint32_t)kDead & 0xFFFFu;
 
     auto retire = [&](bool overflow) {
+        if (bd > 0) {
+            bi = bbase + (31 - ((bkey >> 4) & 31)) * S + (S - 1 - (bkey & 15));
+            bj = bd - bi;
+        }
         if (glane == 0) src.retire(gj, task, overflow, T, bi, bj);
         active = false;
         ng = 0;  // the frame offset stays put while the group waits
@@ -233,11 +238,11 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         // the lowest window slot among the cells holding the maximum.
         const int32_t mkey = __reduce_max_sync(gm, (lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
         const int32_t xm = mkey >> 9;  // best r - thr on the diagonal (-1: none live)
-        const int32_t nbi = (i0 - glane * S) + (31 - ((mkey >> 4) & 31)) * S + (S - 1 - (mkey & 15));
         const bool up = active && xm > sc.x;
         T = up ? T - sc.x + xm : T;
-        bi = up ? nbi : bi;
-        bj = up ? d - nbi : bj;
+        bkey = up ? mkey : bkey;           // decoded at retire
+        bbase = up ? i0 - glane * S : bbase;
+        bd = up ? d : bd;
         const bool dead = (mkey < 0);
         fin = active && ((dead && prev_dead) || d >= m + n);
         prev_dead = dead;
@@ -383,6 +388,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         Q = 0;
                         bi = 0;
                         bj = 0;
+                        bd = 0;
                         prev_dead = false;
                         active = true;
                     }
