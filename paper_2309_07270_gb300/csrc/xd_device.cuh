@@ -842,6 +842,8 @@ __device__ __forceinline__ void serve_list_wide(const ServeArgs &a, const Job *g
 }
 
 constexpr unsigned long long kSpillBacklog = 64;  // ring warps switch tiers above this
+constexpr unsigned long long kDeepBacklog = 16384;  // ring positions: claim chunks above this
+constexpr unsigned long long kClaimChunk = 16;     // positions per claim with a deep backlog
 
 struct RingSrc {
     static constexpr bool kCanAbort = true;  // teardown may stop the loop
@@ -851,8 +853,17 @@ struct RingSrc {
     int level;     // backoff doubling level (leader)
     bool leaving;  // stop, yield or the idle bound (not a switch to the second tier)
 
+    unsigned long long buf_base = 0;  // claimed ring positions not yet handed out (leader)
+    int buf_n = 0;
+
     // Warp-level fetch (see BatchSrc): one poll and one CAS for all the
-    // warp's waiting groups; idle warps back off exponentially.
+    // warp's waiting groups.  Every claimed position is below the published
+    // end, so it holds a task.  With a deep backlog the warp claims a chunk
+    // of kClaimChunk positions and hands the rest to its next waiting
+    // groups from its buffer, which cuts the number of CASes on `consumed`
+    // (under load most of them lose to another warp); a warp with a
+    // non-empty buffer neither switches tiers nor leaves.  A lost CAS race
+    // is retried at the next turn; only an empty ring starts the back-off.
     __device__ __forceinline__ int fetch_warp(unsigned needm, int lane, int gbase, unsigned gm,
                                               bool need, uint32_t &task, const Job *&gj)
     {
@@ -860,7 +871,14 @@ struct RingSrc {
         int k = 0;
         unsigned long long base = 0;
         if (lane == 0) {
-            if (backoff > 0) {
+            const int want = __popc(needm);
+            if (buf_n > 0) {
+                k = buf_n < want ? buf_n : want;
+                base = buf_base;
+                buf_base += (unsigned long long)k;
+                buf_n -= k;
+                status = 1;
+            } else if (backoff > 0) {
                 --backoff;
             } else {
                 volatile ServeCtl *v = a.ctl;
@@ -873,13 +891,16 @@ struct RingSrc {
                 } else {
                     const unsigned long long pub = v->published;
                     unsigned long long cons = *(volatile unsigned long long *)&a.ctl->consumed;
-                    const unsigned long long want = (unsigned long long)__popc(needm);
                     for (int tries = 0; tries < 4 && cons < pub; ++tries) {
-                        const unsigned long long kk = (pub - cons < want) ? pub - cons : want;
+                        const unsigned long long chunk =
+                            (pub - cons > kDeepBacklog) ? kClaimChunk : (unsigned long long)want;
+                        const unsigned long long kk = (pub - cons < chunk) ? pub - cons : chunk;
                         const unsigned long long got = atomicCAS(&a.ctl->consumed, cons, cons + kk);
                         if (got == cons) {
                             base = cons;
-                            k = (int)kk;
+                            k = (kk < (unsigned long long)want) ? (int)kk : want;
+                            buf_base = cons + (unsigned long long)k;
+                            buf_n = (int)kk - k;
                             status = 1;
                             break;
                         }
@@ -888,7 +909,7 @@ struct RingSrc {
                     if (status == 1) {
                         idle_since = 0;
                         level = 0;
-                    } else {
+                    } else if (cons >= pub) {  // nothing published to take
                         const unsigned long long now = globaltimer_ns();
                         if (idle_since == 0) idle_since = now;
                         if (v->stop || now - idle_since > v->idle_ns) status = -1;
