@@ -1,0 +1,73 @@
+"""CPU check of the packed 16-bit band arithmetic against the oracle.
+
+``packed16_model`` restates the kernel's 16-bit arithmetic bit by bit
+(two slots per register, s16x2 ops, normalised and scaled frame, rebases,
+packed keys, window shifts).  On seeded random extensions, including
+scorings at the edges of the packed range, it must reach the oracle's
+(score, best_i, best_j) exactly whenever the band fits the window, and no
+16-bit half may ever wrap.  This pins the exactness argument of the packed
+tiles without a GPU; the GPU tests pin the kernel itself.
+"""
+import numpy as np
+import pytest
+
+import packed16_model as P
+from paper_2309_07270_gb300 import workloads as W
+
+SCORINGS = [
+    (1, -1, -1, 50),
+    (1, 0, -1, 20),         # mismatch + 2|gap| > 0, many ties
+    (2, -3, -2, 30),
+    (64, -128, -64, 1472),  # every limit at once
+    (3, -2, -125, 100),     # the frame grows fastest through the gap
+    (127, -1, -1, 1409),    # largest match
+    (1, -128, -1, 1535),    # largest x
+    (7, -1, -2, 0),         # x = 0
+]
+
+
+def cases(seed, n):
+    rng = np.random.default_rng(seed)
+    for k in range(n):
+        sc = SCORINGS[k % len(SCORINGS)]
+        la, lb = int(rng.integers(0, 260)), int(rng.integers(0, 260))
+        t = rng.integers(0, 4, max(la, lb) + 40).astype(np.uint8)
+        kind = k % 3
+        if kind == 0:    # related: the second read mutated at 12 %
+            b, *_ = W.mutate(t, rng)
+            yield sc, t[:la], b[:lb]
+        elif kind == 1:  # unrelated
+            yield sc, rng.integers(0, 4, la).astype(np.uint8), rng.integers(0, 4, lb).astype(np.uint8)
+        else:            # identical prefixes
+            yield sc, t[:la], t[:lb].copy()
+
+
+def test_scorings_are_in_the_packed_range():
+    assert all(P.fits(*sc) for sc in SCORINGS)
+    assert not P.fits(1, -1, -1, 1536) and not P.fits(128, -1, -1, 10)
+    assert not P.fits(1, -129, -1, 10) and not P.fits(1, -1, -128, 10)
+
+
+@pytest.mark.parametrize("lanes,regs,seed", [(4, 8, 1), (8, 4, 2)])
+def test_model_matches_oracle(orc, lanes, regs, seed):
+    done = overflow = 0
+    for sc, a, b in cases(seed, 48):
+        want = orc.extend(a, b, *sc)[:3]
+        got = P.extend(a, b, *sc, lanes=lanes, regs=regs)
+        if got[3]:
+            overflow += 1
+            continue
+        assert tuple(got[:3]) == tuple(want), (sc, len(a), len(b), got, want)
+        done += 1
+    assert done >= 30 and overflow <= 18
+
+
+def test_model_long_identical_reads_rebase_many_times(orc):
+    """Identical 1,500-base reads with the largest match: the score
+    grows by 127 per diagonal pair, so the frame is rebased over and over."""
+    rng = np.random.default_rng(9)
+    t = rng.integers(0, 4, 1500).astype(np.uint8)
+    for sc in [(127, -1, -1, 1409), (64, -128, -64, 1472)]:
+        want = orc.extend(t, t, *sc)[:3]
+        got = P.extend(t, t, *sc, lanes=4, regs=8)
+        assert not got[3] and tuple(got[:3]) == tuple(want), (sc, got, want)
