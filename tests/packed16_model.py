@@ -75,13 +75,18 @@ def fits(match, mismatch, gap, x):
     return match - gap <= 128 and mismatch >= -128 and x >= 0 and x + match <= 1536
 
 
-def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8):
+def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
     """One extension over base codes a (length m) and b (length n) on a
     group of `lanes` lanes with `regs` registers (2*regs slots) per lane.
 
     Returns (score, best_i, best_j, overflow); with overflow True the
     kernel would hand the task to a wider tier and the other fields are
-    meaningless."""
+    meaningless.  ``stats`` (a dict) receives counts of window shifts up
+    and down, rebases and masked diagonals."""
+    if stats is None:
+        stats = {}
+    for k in ("up", "down", "rebase", "masked"):
+        stats.setdefault(k, 0)
     C2, S = regs, 2 * regs
     W = lanes * S
     m, n = len(a), len(b)
@@ -126,6 +131,7 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8):
             if not masked and margin() < 0:
                 raise AssertionError("unmasked diagonal leaves the rectangle")
             V, U = (O, E) if odd else (E, O)
+            stats["masked"] += masked
             nthr2 = pack2(-SCALE * (T + Q))
             lane_keys = []
             for g in range(lanes):
@@ -176,10 +182,15 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8):
             fin = (dead and prev_dead) or d >= m + n
             prev_dead = dead
             dead16 = DEAD & 0xFFFF
+            # window edges: after an odd diagonal a live top slot may seed a
+            # cell above the window (shift up), after an even one a live
+            # bottom slot one below it (shift down); with the opposite edge
+            # live too the band outgrew the window
             vtop, vbot = V[lanes - 1][C2 - 1] >> 16, V[0][0] & 0xFFFF
             if not fin and (vtop if odd else vbot) != dead16:
                 if (vbot if odd else vtop) != dead16:
                     return T, 0, 0, True
+                stats["up" if odd else "down"] += 1
                 if odd:  # shift up: slot s takes slot s+1
                     ne = [E[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
                     no = [O[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
@@ -206,6 +217,7 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8):
                 return T, bi, bd - bi, False
             if not odd:
                 if T + Q + ng >= REBASE:
+                    stats["rebase"] += 1
                     mr = pack2(-SCALE * REBASE)
                     for g in range(lanes):
                         for t in range(C2):

@@ -71,3 +71,33 @@ def test_model_long_identical_reads_rebase_many_times(orc):
         want = orc.extend(t, t, *sc)[:3]
         got = P.extend(t, t, *sc, lanes=4, regs=8)
         assert not got[3] and tuple(got[:3]) == tuple(want), (sc, got, want)
+
+
+def _drifting(t, rng, every):
+    """t with one random base inserted after every `every` bases."""
+    out = []
+    for k in range(0, len(t), every):
+        out.append(t[k:k + every])
+        out.append(rng.integers(0, 4, 1).astype(np.uint8))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("lanes,regs", [(4, 8), (2, 8)])
+def test_model_drifting_band_shifts_the_window(orc, lanes, regs):
+    """One read gains a base every 8 (then the other does): the optimal
+    path drifts one diagonal per 8 bases, so the window must shift many
+    slots up in one case and down in the other while the band stays
+    narrow."""
+    rng = np.random.default_rng(17)
+    t = rng.integers(0, 4, 480).astype(np.uint8)
+    d = _drifting(t, rng, 8)
+    shifted = {"up": 0, "down": 0}
+    for a, b in [(t, d), (d, t)]:
+        for sc in [(1, -1, -1, 20), (2, -3, -1, 30)]:
+            st = {}
+            got = P.extend(a, b, *sc, lanes=lanes, regs=regs, stats=st)
+            assert not got[3], (sc, lanes, regs)
+            assert tuple(got[:3]) == tuple(orc.extend(a, b, *sc)[:3]), (sc, lanes, regs, got)
+            shifted["up"] += st["up"]
+            shifted["down"] += st["down"]
+    assert shifted["up"] >= 8 and shifted["down"] >= 8, shifted
