@@ -179,8 +179,10 @@ static int align_one(const uint32_t *packed, const uint64_t *read_off,
 {
     memset(o, 0, sizeof(*o));
     if (cells2) { cells2[0] = 0; cells2[1] = 0; }
-    if (p->a >= n_reads || p->b >= n_reads) { o->status = 1; return -1; }
-    uint64_t la = read_len[p->a], lb = read_len[p->b];
+    const uint32_t rb = p->b & ~ORC_PAIR_RC;  /* read id of b */
+    const int rc = (p->b & ORC_PAIR_RC) != 0;
+    if (p->a >= n_reads || rb >= n_reads) { o->status = 1; return -1; }
+    uint64_t la = read_len[p->a], lb = read_len[rb];
     if ((uint64_t)p->seed_a + p->seed_len > la ||
         (uint64_t)p->seed_b + p->seed_len > lb) {
         o->status = 1;
@@ -201,7 +203,15 @@ static int align_one(const uint32_t *packed, const uint64_t *read_off,
         return -1;
     }
     orc_unpack(packed, read_off[p->a], la, A);
-    orc_unpack(packed, read_off[p->b], lb, B);
+    orc_unpack(packed, read_off[rb], lb, B);
+    if (rc) {  /* the reverse complement of read b, written out */
+        for (uint64_t k = 0; k < lb / 2; ++k) {
+            const uint8_t t = B[k];
+            B[k] = B[lb - 1 - k];
+            B[lb - 1 - k] = t;
+        }
+        for (uint64_t k = 0; k < lb; ++k) B[k] = (uint8_t)(3 - B[k]);
+    }
 
     int32_t sc_out;
     int64_t bi, bj, c;

@@ -31,8 +31,17 @@ typedef struct {
     int32_t x;        /* the X-drop threshold, >= 0                      */
 } orc_scoring;
 
+/* b's top bit (ORC_PAIR_RC) selects the reverse strand of read b: the
+ * pair aligns read a against the reverse complement of read b (base k of
+ * it is the complement, code 3 - c, of base len_b - 1 - k of read b), and
+ * seed_b and the reported b coordinates are positions in that reverse
+ * complement.  The paper's reads come from both strands (overlaps of
+ * long reads, Section "Method"); it does not spell out the strand step,
+ * so this is the reading the oracle fixes. */
+#define ORC_PAIR_RC 0x80000000u
+
 typedef struct {
-    uint32_t a, b;           /* read ids                                  */
+    uint32_t a, b;           /* read ids (b may carry ORC_PAIR_RC)        */
     uint32_t seed_a, seed_b; /* 0-based start of the exact seed on a / b */
     uint32_t seed_len;       /* seed length in bases                      */
 } orc_pair;

@@ -28,6 +28,7 @@ PAIR_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("seed_a", "<u4"),
                        ("seed_b", "<u4"), ("seed_len", "<u4")])
 SEED_LEN = 17
 PACK_TAIL_WORDS = 64
+PAIR_RC = 0x80000000  # in a pair's b: align against the reverse complement of read b
 P_SUB, P_DEL, P_INS = 0.04, 0.04, 0.04
 _CHUNK = 1 << 24
 
@@ -473,3 +474,30 @@ ACGT = "ACGT"
 def encode(s: str) -> np.ndarray:
     """Codes of an ACGT string."""
     return np.array([ACGT.index(ch) for ch in s], dtype=np.uint8)
+
+
+def revcomp(codes: np.ndarray) -> np.ndarray:
+    """Reverse complement of a code array (A=0, C=1, G=2, T=3)."""
+    return (3 - np.asarray(codes, dtype=np.uint8)[::-1]).astype(np.uint8)
+
+
+def reverse_strand(w: Workload, frac: float = 0.5, seed: int = 0) -> Workload:
+    """The same alignments with a fraction of the pairs on the reverse
+    strand: for each chosen pair the reverse complement of its read b is
+    stored as a new read, and the pair points at that read with PAIR_RC
+    set.  Aligning against the reverse complement of the stored read gives
+    back read b, so every result must equal the original workload's."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pairs = w.pairs.copy()
+    pick = np.flatnonzero(rng.random(len(pairs)) < frac)
+    reads = [w.codes(r) for r in range(len(w.read_len))]
+    rc_of = {}
+    for p in pick:
+        b = int(pairs["b"][p])
+        if b not in rc_of:
+            rc_of[b] = len(reads)
+            reads.append(revcomp(reads[b]))
+        pairs["b"][p] = np.uint32(rc_of[b] | PAIR_RC)
+    packed, off, lens = pack_reads(reads)
+    return dataclasses.replace(w, packed=packed, read_off=off, read_len=lens.astype(np.uint32),
+                               pairs=pairs, name=f"{w.name}-rc{frac:g}")

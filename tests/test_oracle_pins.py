@@ -239,6 +239,35 @@ def test_pair_coordinates(orc):
     assert tuple(int(v) for v in res[0]) == (1, 1, 0, 2, 6, 5, 0)
 
 
+def test_reverse_strand_hand_case(orc):
+    """Read b stored as CGTTGCAA is the reverse complement of a = TTGCAACG:
+    with PAIR_RC the pair aligns a against TTGCAACG itself, so both
+    extensions are exact (3 bases each).  Reversing only (AACGTTGC) or
+    complementing only (GCAACGTT) would leave mismatches."""
+    wl = W.from_sequences([W.encode("TTGCAACG")], [W.encode("CGTTGCAA")], [(3, 3, 2)], x=5)
+    wl.pairs["b"] |= np.uint32(W.PAIR_RC)
+    res = orc.align_pairs(wl.packed, wl.read_off, wl.read_len, wl.pairs, 1, -1, -1, 5)
+    assert tuple(int(v) for v in res[0]) == (3, 0, 0, 3, 8, 8, 0)
+    assert W.encode("CGTTGCAA").tolist() == W.revcomp(W.encode("TTGCAACG")).tolist()
+
+
+def test_reverse_strand_pairs_equal_forward(orc):
+    """Storing read b reverse-complemented and flagging the pair gives back
+    the forward alignment exactly; without the flag it does not."""
+    w = W.template_pairs(n_pairs=30, len_lo=300, len_hi=900, seed=4)
+    r = W.reverse_strand(w, 0.5, 1)
+    assert (r.pairs["b"] >> 31).sum() >= 10
+    fwd = orc.align_pairs(w.packed, w.read_off, w.read_len, w.pairs, 1, -1, -1, 50)
+    got = orc.align_pairs(r.packed, r.read_off, r.read_len, r.pairs, 1, -1, -1, 50)
+    assert np.array_equal(fwd.view(np.int32), got.view(np.int32))
+    unflagged = r.pairs.copy()
+    unflagged["b"] &= np.uint32(0x7FFFFFFF)
+    off = orc.align_pairs(r.packed, r.read_off, r.read_len, unflagged, 1, -1, -1, 50)
+    flipped = (r.pairs["b"] >> 31) == 1
+    assert not np.array_equal(fwd.view(np.int32).reshape(-1, 7)[flipped],
+                              off.view(np.int32).reshape(-1, 7)[flipped])
+
+
 def test_left_is_reversed_right(orc):
     w = W.tiny_pairs(n_pairs=24, seed=5, x=15)
     res, cells = orc.align_pairs(w.packed, w.read_off, w.read_len, w.pairs, 1, -1, -1, 15,
