@@ -73,8 +73,18 @@ typedef struct {
     int32_t match, mismatch, gap, x;
 } xdrop_scoring;
 
+/* Reverse strand: set in a pair's b to align read a against the reverse
+ * complement of read (b & ~XDROP_PAIR_RC), whose base k is the complement
+ * (code 3 - c) of base len_b - 1 - k of the read; seed_b and the result's
+ * b coordinates are positions in that reverse complement.  Accepted by
+ * xdrop_submit and by xdrop_submit_pairs (resident reads, serving too):
+ * the library stores the reverse complements of the reads beside them.
+ * xdrop_submit_device, xdrop_count_cells_device and xdrop_align_static
+ * give such a pair XDROP_STATUS_INVALID. */
+#define XDROP_PAIR_RC 0x80000000u
+
 typedef struct {
-    uint32_t a, b;           /* read ids                          */
+    uint32_t a, b;           /* read ids (b may carry XDROP_PAIR_RC) */
     uint32_t seed_a, seed_b; /* 0-based seed start on each read   */
     uint32_t seed_len;       /* seed length in bases              */
 } xdrop_pair;                /* 20 bytes, no padding              */

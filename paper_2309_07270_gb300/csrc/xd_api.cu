@@ -538,18 +538,21 @@ int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
     }
     if (n_words * 16 >= ((uint64_t)1 << 32)) return fail(XDROP_EINVAL, "packed buffer too large");
     const Scoring sc{s->match, s->mismatch, s->gap, s->x};
+    bool any_rc = false;  // reverse-strand pairs: store the reverse complements too
     for (size_t p = 0; p < n_pairs; ++p) {
         const Pair &pr = *(const Pair *)&pairs[p];
-        if (!pair_ok(pr, n_reads, read_len, read_off, (int64_t)n_words, sc))
+        if (!pair_ok(pr, n_reads, read_len, read_off, (int64_t)n_words, sc, true))
             return fail(XDROP_EINVAL, "pair %zu is invalid (read id, seed or length limit)", p);
+        any_rc |= (pr.b & kPairRC) != 0;
     }
+    const uint64_t pk_words = any_rc ? 2 * n_words : n_words;
     std::lock_guard<std::mutex> lk(c->mu);
     CK(cudaSetDevice(c->device));
     Ticket *tk = nullptr;
     if ((rc = new_ticket(c, n_pairs, false, &tk))) return rc;
     tk->out = out;
     // One device allocation for the inputs and results of this ticket.
-    size_t o_packed = 0, o_off = align_up(std::max<uint64_t>(n_words, 1) * 4);
+    size_t o_packed = 0, o_off = align_up(std::max<uint64_t>(pk_words, 1) * 4);
     size_t o_len = o_off + align_up((size_t)std::max(n_reads, 1u) * 8);
     size_t o_pairs = o_len + align_up((size_t)std::max(n_reads, 1u) * 4);
     size_t o_out = o_pairs + align_up(std::max<size_t>(n_pairs, 1) * sizeof(xdrop_pair));
@@ -579,6 +582,12 @@ int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && n_pairs)
         e = cudaMemsetAsync(d + o_out, 0, n_pairs * sizeof(xdrop_result), st);
+    if (e == cudaSuccess && any_rc) {
+        e = launch_revcomp((const uint32_t *)(d + o_packed), (int64_t)n_words,
+                           (const uint64_t *)(d + o_off), (const uint32_t *)(d + o_len), n_reads,
+                           (uint32_t *)(d + o_packed) + n_words, st);
+        if (e == cudaSuccess) tk->launches += 1;
+    }
     if (e != cudaSuccess) {
         cudaStreamSynchronize(st);
         free_ticket(c, tk);
@@ -586,7 +595,8 @@ int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
     }
     Job job{};
     job.packed = (const uint32_t *)(d + o_packed);
-    job.n_words = (int64_t)std::max<uint64_t>(n_words, 1);
+    job.n_words = (int64_t)std::max<uint64_t>(pk_words, 1);
+    job.rc_off = any_rc ? (int64_t)(16 * n_words) : 0;
     job.read_off = (const uint64_t *)(d + o_off);
     job.read_len = (const uint32_t *)(d + o_len);
     job.n_reads = n_reads;
@@ -781,13 +791,18 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
     CK(cudaStreamSynchronize(c->stream));
     int rc;
     const uint64_t nw = std::max<uint64_t>(n_words, 1);
-    if ((rc = dev_alloc(c, c->r_packed, nw * 4))) return rc;
+    // the reads, then their reverse complements (reverse-strand pairs)
+    if ((rc = dev_alloc(c, c->r_packed, 2 * nw * 4))) return rc;
     if ((rc = dev_alloc(c, c->r_off, std::max<size_t>(n_reads, 1) * 8))) return rc;
     if ((rc = dev_alloc(c, c->r_len, std::max<size_t>(n_reads, 1) * 4))) return rc;
     if (n_words) CK(cudaMemcpy(c->r_packed.p, packed, n_words * 4, cudaMemcpyHostToDevice));
     if (n_reads) {
         CK(cudaMemcpy(c->r_off.p, read_off, (size_t)n_reads * 8, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->r_len.p, read_len, (size_t)n_reads * 4, cudaMemcpyHostToDevice));
+        CK(launch_revcomp((const uint32_t *)c->r_packed.p, (int64_t)nw, (const uint64_t *)c->r_off.p,
+                          (const uint32_t *)c->r_len.p, n_reads, (uint32_t *)c->r_packed.p + nw,
+                          c->stream));
+        CK(cudaStreamSynchronize(c->stream));
     }
     c->h_off.assign(read_off, read_off + n_reads);
     c->h_len.assign(read_len, read_len + n_reads);
@@ -799,7 +814,8 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
     if (c->mode == XDROP_MODE_SERVE) {
         xd::ResidentReads rr;
         rr.packed = (const uint32_t *)c->r_packed.p;
-        rr.n_words = (int64_t)nw;
+        rr.n_words = (int64_t)(2 * nw);
+        rr.rc_off = (int64_t)(16 * nw);
         rr.read_off = (const uint64_t *)c->r_off.p;
         rr.read_len = (const uint32_t *)c->r_len.p;
         rr.n_reads = n_reads;
@@ -830,7 +846,7 @@ int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
         if (!c->have_reads) return fail(XDROP_EINVAL, "no resident reads (xdrop_load_reads)");
         for (size_t p = 0; p < n_pairs; ++p) {
             const Pair &pr = *(const Pair *)&pairs[p];
-            if (!pair_ok(pr, c->r_n, c->h_len.data(), c->h_off.data(), (int64_t)c->r_words, sc))
+            if (!pair_ok(pr, c->r_n, c->h_len.data(), c->h_off.data(), (int64_t)c->r_words, sc, true))
                 return fail(XDROP_EINVAL, "pair %zu is invalid (read id, seed or length limit)", p);
         }
         srv = c->srv;
@@ -895,7 +911,8 @@ int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
     if (n_chunks > 1) {
         Job base{};
         base.packed = (const uint32_t *)c->r_packed.p;
-        base.n_words = (int64_t)c->r_words;
+        base.n_words = (int64_t)(2 * c->r_words);
+        base.rc_off = (int64_t)(16 * c->r_words);
         base.read_off = (const uint64_t *)c->r_off.p;
         base.read_len = (const uint32_t *)c->r_len.p;
         base.n_reads = c->r_n;
@@ -921,7 +938,8 @@ int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
     }
     Job job{};
     job.packed = (const uint32_t *)c->r_packed.p;
-    job.n_words = (int64_t)c->r_words;
+    job.n_words = (int64_t)(2 * c->r_words);
+    job.rc_off = (int64_t)(16 * c->r_words);
     job.read_off = (const uint64_t *)c->r_off.p;
     job.read_len = (const uint32_t *)c->r_len.p;
     job.n_reads = c->r_n;

@@ -43,6 +43,11 @@ cudaError_t launch_validate(const Job *jp, uint64_t n_pairs, uint32_t *n_bad, cu
 cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *hist,
                            uint32_t *offs, uint32_t *n_valid, uint32_t *order,
                            cudaStream_t s);
+// Reverse complement of every read of `pk` (n_words words) into `out`, at
+// the same offsets (reverse-strand pairs).
+cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *read_off,
+                           const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
+                           cudaStream_t s);
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s);
 

@@ -14,7 +14,7 @@ __global__ void validate_kernel(const Job *jp, uint32_t *n_bad)
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < J.n_pairs;
          p += (uint64_t)gridDim.x * blockDim.x) {
         const Pair pr = J.pairs[p];
-        const bool ok = pair_ok(pr, J.n_reads, J.read_len, J.read_off, J.n_words, J.sc);
+        const bool ok = job_pair_ok(J, pr);
         int32_t *o = J.out + p * 7;
         if (!ok) {
             for (int k = 0; k < 6; ++k) o[k] = 0;
@@ -113,6 +113,26 @@ __global__ void max_len_kernel(const uint32_t *read_len, uint32_t n_reads, uint3
         m = max(m, read_len[r]);
     m = __reduce_max_sync(FULL, m);
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// ---------------------------------------------------------------------------
+// Reverse complements of all reads (reverse-strand pairs): read r's reverse
+// complement goes to the same word offsets of `out`.  Output base p of the
+// read is the complement (code ^ 3) of input base len - 1 - p, so output
+// word w is the reversed, complemented 16 input bases ending at len - 16 w;
+// bases past the read's end in its last word are left arbitrary.
+// ---------------------------------------------------------------------------
+__global__ void revcomp_kernel(const uint32_t *pk, int64_t n_words, const uint64_t *read_off,
+                               const uint32_t *read_len, uint32_t n_reads, uint32_t *out)
+{
+    for (uint32_t r = blockIdx.x; r < n_reads; r += gridDim.x) {
+        const int64_t off = (int64_t)read_off[r];
+        const int64_t len = (int64_t)read_len[r];
+        const int64_t w0 = off >> 4;
+        const int64_t nwr = (len + 15) >> 4;
+        for (int64_t w = threadIdx.x; w < nwr; w += blockDim.x)
+            out[w0 + w] = rev16(load16_u(pk, n_words, off + len - 16 * (w + 1))) ^ 0xFFFFFFFFu;
+    }
 }
 
 }  // namespace xd

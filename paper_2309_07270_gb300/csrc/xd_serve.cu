@@ -269,7 +269,7 @@ bool Server::admit(Req *r)
             uint32_t m, n;
             if (t & 1) {
                 m = rr_len_host[p.a] - p.seed_a - p.seed_len;
-                n = rr_len_host[p.b] - p.seed_b - p.seed_len;
+                n = rr_len_host[p.b & ~kPairRC] - p.seed_b - p.seed_len;
             } else {
                 m = p.seed_a;
                 n = p.seed_b;
@@ -285,6 +285,7 @@ bool Server::admit(Req *r)
     Job *job = (Job *)(h + r->h_job);
     job->packed = rr.packed;
     job->n_words = rr.n_words;
+    job->rc_off = rr.rc_off;
     job->read_off = rr.read_off;
     job->read_len = rr.read_len;
     job->n_reads = rr.n_reads;

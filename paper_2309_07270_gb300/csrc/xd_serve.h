@@ -13,8 +13,9 @@ namespace xd {
 
 // Reads resident on the device (shared by every request).
 struct ResidentReads {
-    const uint32_t *packed = nullptr;  // device
-    int64_t n_words = 0;
+    const uint32_t *packed = nullptr;  // device: the reads, then their reverse complements
+    int64_t n_words = 0;               // words of the whole buffer
+    int64_t rc_off = 0;                // bases from a read to its reverse complement
     const uint64_t *read_off = nullptr;  // device
     const uint32_t *read_len = nullptr;  // device
     uint32_t n_reads = 0;

@@ -60,6 +60,17 @@ cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *
     return cudaGetLastError();
 }
 
+cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *read_off,
+                           const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
+                           cudaStream_t s)
+{
+    if (!n_reads) return cudaSuccess;
+    (void)cudaGetLastError();
+    const unsigned grid = n_reads < 4096u ? n_reads : 4096u;
+    revcomp_kernel<<<grid, 128, 0, s>>>(pk, n_words, read_off, read_len, n_reads, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s)
 {

@@ -22,9 +22,16 @@ struct Scoring {
 
 // Everything a kernel needs to decode and write one task.  Task t is the
 // left (t even) or right (t odd) extension of pair t/2.
+// Top bit of a pair's b: align against the reverse complement of read b
+// (XDROP_PAIR_RC).  The library stores the reverse complement of every
+// read after the reads themselves, rc_off bases further on, and an RC pair
+// reads its b there; the band kernels never see the flag.
+constexpr uint32_t kPairRC = 0x80000000u;
+
 struct Job {
-    const uint32_t *packed;
-    int64_t n_words;
+    const uint32_t *packed;  // the reads, then (rc_off > 0) their reverse complements
+    int64_t n_words;         // words of the whole buffer
+    int64_t rc_off;          // bases from a read to its reverse complement; 0 = none stored
     const uint64_t *read_off;
     const uint32_t *read_len;
     uint32_t n_reads;
@@ -93,22 +100,32 @@ __host__ __device__ inline int32_t max_abs_score(const Scoring &s)
     return m > c ? m : c;
 }
 
+// n_words: words of the reads themselves (without reverse complements);
+// rc_ok: whether a pair may ask for the reverse strand of b.
 __host__ __device__ inline bool pair_ok(const Pair &p, uint32_t n_reads,
                                         const uint32_t *read_len,
                                         const uint64_t *read_off,
-                                        int64_t n_words, const Scoring &s)
+                                        int64_t n_words, const Scoring &s, bool rc_ok)
 {
-    if (p.a >= n_reads || p.b >= n_reads) return false;
-    uint64_t la = read_len[p.a], lb = read_len[p.b];
+    const uint32_t b = p.b & ~kPairRC;
+    if ((p.b & kPairRC) && !rc_ok) return false;
+    if (p.a >= n_reads || b >= n_reads) return false;
+    uint64_t la = read_len[p.a], lb = read_len[b];
     if ((int64_t)la >= LEN_LIMIT || (int64_t)lb >= LEN_LIMIT) return false;
     if ((uint64_t)p.seed_a + p.seed_len > la) return false;
     if ((uint64_t)p.seed_b + p.seed_len > lb) return false;
     if ((int64_t)(la + lb) * max_abs_score(s) >= SCORE_LIMIT) return false;
-    uint64_t oa = read_off[p.a], ob = read_off[p.b];
+    uint64_t oa = read_off[p.a], ob = read_off[b];
     if ((oa & 15) || (ob & 15)) return false;
     if ((int64_t)((oa + la + 15) / 16) > n_words) return false;
     if ((int64_t)((ob + lb + 15) / 16) > n_words) return false;
     return true;
+}
+
+__host__ __device__ inline bool job_pair_ok(const Job &J, const Pair &p)
+{
+    return pair_ok(p, J.n_reads, J.read_len, J.read_off, J.rc_off ? J.rc_off / 16 : J.n_words,
+                   J.sc, J.rc_off > 0);
 }
 
 __device__ __forceinline__ Ext decode(const Job &J, uint32_t task)
@@ -117,7 +134,7 @@ __device__ __forceinline__ Ext decode(const Job &J, uint32_t task)
     e.pair = task >> 1;
     e.side = (int)(task & 1u);
     Pair p = J.pairs[e.pair];
-    e.ok = pair_ok(p, J.n_reads, J.read_len, J.read_off, J.n_words, J.sc);
+    e.ok = job_pair_ok(J, p);
     e.sa = p.seed_a;
     e.sb = p.seed_b;
     e.L = p.seed_len;
@@ -127,8 +144,10 @@ __device__ __forceinline__ Ext decode(const Job &J, uint32_t task)
     e.A.s0 = e.B.s0 = 0;
     e.A.dir = e.B.dir = 1;
     if (!e.ok) return e;
-    int64_t oa = (int64_t)J.read_off[p.a], ob = (int64_t)J.read_off[p.b];
-    int64_t la = J.read_len[p.a], lb = J.read_len[p.b];
+    const uint32_t b = p.b & ~kPairRC;
+    int64_t oa = (int64_t)J.read_off[p.a];
+    int64_t ob = (int64_t)J.read_off[b] + ((p.b & kPairRC) ? J.rc_off : 0);
+    int64_t la = J.read_len[p.a], lb = J.read_len[b];
     if (e.side) {  // right: c_k = X[seed + L + k - 1]
         e.m = (int32_t)(la - p.seed_a - p.seed_len);
         e.n = (int32_t)(lb - p.seed_b - p.seed_len);

@@ -28,6 +28,7 @@ XDROP_STATUS_OK = 0
 XDROP_STATUS_INVALID = 1
 XDROP_STATUS_TOO_LONG = 2
 XDROP_TILE_PACKED16 = 0x100  # xdrop_set_tile: 16-bit packed tile
+XDROP_PAIR_RC = 0x80000000   # in a pair's b: the reverse strand of read b
 
 PAIR_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("seed_a", "<u4"),
                        ("seed_b", "<u4"), ("seed_len", "<u4")])

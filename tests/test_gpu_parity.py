@@ -294,3 +294,36 @@ def test_genome_29x_every_pair_every_tile(X, orc, genome29, x):
         want = oracle_results(orc, w.subset(idx[:50]), nthreads=16).view(np.int32).reshape(-1, 7)
         wrong = {tile_id(t): int((res[t][idx[:50]] != want).any(axis=1).sum()) for t in tiles}
         pytest.fail(f"{idx.size} pairs differ between tiles; wrong of the first 50: {wrong}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_reverse_strand_pairs(X, aligners, orc, mode):
+    """Half the pairs on the reverse strand (read b stored reverse-
+    complemented, XDROP_PAIR_RC set): identical to the oracle and to the
+    forward workload's results."""
+    w = W.template_pairs(n_pairs=60, len_lo=500, len_hi=2500, seed=41)
+    r = W.reverse_strand(w, 0.5, 3)
+    got = run_host(X, aligners[mode], r)
+    assert_same(got, oracle_results(orc, r), f"{mode} reverse strand")
+    assert np.array_equal(got.view(np.int32), run_host(X, aligners[mode], w).view(np.int32))
+
+
+def test_reverse_strand_resident_reads_and_device_submit(X, orc):
+    """Over resident reads (xdrop_submit_pairs) reverse-strand pairs are
+    exact; a device submit marks them invalid and keeps the others exact."""
+    w = W.reverse_strand(W.template_pairs(n_pairs=40, len_lo=500, len_hi=2000, seed=42), 0.5, 4)
+    sc = X.scoring(1, -1, -1, 50)
+    rcm = (w.pairs["b"] >> 31) == 1
+    assert rcm.sum() >= 10
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        X.xdrop_load_reads(al.ctx, w.packed, w.read_off, w.read_len)
+        out = np.zeros(w.n_pairs, X.RESULT_DTYPE)
+        X.xdrop_sync(al.ctx, X.xdrop_submit_pairs(al.ctx, w.pairs, sc, out))
+        assert_same(out, oracle_results(orc, w), "resident reverse strand")
+        dev = X.DeviceInputs.from_workload(w)
+        with pytest.raises(X.XdropError) as ei:
+            al.align_device(dev, sc)
+        assert ei.value.code == X.XDROP_EINVAL
+        res = dev.results()
+    assert (res["status"][rcm] == X.XDROP_STATUS_INVALID).all()
+    assert_same(res[~rcm], oracle_results(orc, w.subset(np.flatnonzero(~rcm))), "device forward")

@@ -222,3 +222,18 @@ def test_mixed_scorings_packed_and_not(X, orc, pool):
         want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
                                *scs[p % 2], nthreads=8)
         assert np.array_equal(outs[i].view(np.int32), want.view(np.int32)), (i, scs[p % 2])
+
+
+def test_reverse_strand_requests(X, orc):
+    """Serving requests with reverse-strand pairs equal the oracle."""
+    w = W.reverse_strand(W.template_pairs(n_pairs=120, len_lo=500, len_hi=3000, seed=43), 0.5, 5)
+    sc = X.scoring(1, -1, -1, 50)
+    ctx = serve_ctx(X, w)
+    try:
+        outs = run_alone(X, ctx, w, [(0, np.arange(0, 60)), (1, np.arange(60, 120))], sc)
+    finally:
+        X.xdrop_free(ctx)
+    for k, idx in enumerate([np.arange(0, 60), np.arange(60, 120)]):
+        want = orc.align_pairs(w.packed, w.read_off, w.read_len, w.pairs[idx], 1, -1, -1, 50,
+                               nthreads=8)
+        assert np.array_equal(outs[k].view(np.int32), want.view(np.int32))
