@@ -224,8 +224,8 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
  * scoring (the packed tiles on a third of it when the scoring fits them,
  * else the 32-bit tiles on an eighth) and keeps the fastest for that
  * scoring.  Tiles: 4x16, 8x8, 16x4,
- * 8x16, 16x8, 32x4, and packed (cells | XDROP_TILE_PACKED16) 4x16, 8x8,
- * 8x16, 16x8.  Returns XDROP_EINVAL for another shape.  Serving mode
+ * 8x16, 16x8, 32x4, and packed (cells | XDROP_TILE_PACKED16) 4x8, 2x16,
+ * 4x16, 8x8, 8x16, 16x8.  Returns XDROP_EINVAL for another shape.  Serving mode
  * (set the tile before the first xdrop_submit_pairs) runs packed 4x16 by
  * default; with a packed first tier, requests whose scoring does not fit
  * 16 bits run on the serving kernel's 32-bit second tier. */

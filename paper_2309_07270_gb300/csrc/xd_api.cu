@@ -250,7 +250,8 @@ int enqueue_batched(xdrop_ctx *c, Tile t0, int bps, bool main_events, uint32_t *
 // Candidate first tiles for autotuning (all persistent instantiations);
 // the packed 16-bit ones only for scorings they hold exactly.
 const Tile kTuneTiles[] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4}};
-const Tile kPackedTiles[] = {{4, 16, true}, {8, 8, true}, {8, 16, true}, {16, 8, true}};
+const Tile kPackedTiles[] = {{4, 8, true},  {2, 16, true}, {4, 16, true},
+                             {8, 8, true},  {8, 16, true}, {16, 8, true}};
 
 // The first tile for a submit: the forced one (unpacked when the scoring
 // does not fit 16 bits) or the tuned one for this scoring.

@@ -1,5 +1,6 @@
-// Packed 16-bit band tiles (two window slots per register): 4x16 and 8x8
-// (width 64), 8x16 and 16x8 (width 128).
+// Packed 16-bit band tiles (two window slots per register): 4x8 and 2x16
+// (width 32, narrow bands such as x = 15), 4x16 and 8x8 (width 64), 8x16
+// and 16x8 (width 128).
 #include "xd_launch.h"
 #include "xd_lockstep16.cuh"
 
@@ -28,6 +29,8 @@ cudaError_t launch_persistent_packed(Tile t, int grid, const Job *jp, const uint
 {
     *handled = true;
     if (t.packed) {
+        if (t.lanes == 4 && t.c == 8) return packed_impl<4, 4>(grid, jp, order, n, ctr, sp, s);
+        if (t.lanes == 2 && t.c == 16) return packed_impl<2, 8>(grid, jp, order, n, ctr, sp, s);
         if (t.lanes == 4 && t.c == 16) return packed_impl<4, 8>(grid, jp, order, n, ctr, sp, s);
         if (t.lanes == 8 && t.c == 8) return packed_impl<8, 4>(grid, jp, order, n, ctr, sp, s);
         if (t.lanes == 8 && t.c == 16) return packed_impl<8, 8>(grid, jp, order, n, ctr, sp, s);
@@ -40,6 +43,8 @@ cudaError_t launch_persistent_packed(Tile t, int grid, const Job *jp, const uint
 int occupancy_packed(Tile t)
 {
     if (!t.packed) return -1;
+    if (t.lanes == 4 && t.c == 8) return packed_occupancy_impl<4, 4>();
+    if (t.lanes == 2 && t.c == 16) return packed_occupancy_impl<2, 8>();
     if (t.lanes == 4 && t.c == 16) return packed_occupancy_impl<4, 8>();
     if (t.lanes == 8 && t.c == 8) return packed_occupancy_impl<8, 4>();
     if (t.lanes == 8 && t.c == 16) return packed_occupancy_impl<8, 8>();

@@ -108,7 +108,7 @@ def test_other_scorings(X, aligners, orc, mode, scores):
 
 P16 = 0x100  # XDROP_TILE_PACKED16
 TILES = [(4, 16), (8, 8), (16, 4), (8, 16), (16, 8), (32, 4),
-         (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16)]
+         (4, 8 | P16), (2, 16 | P16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16)]
 
 
 def tile_id(t):
@@ -277,7 +277,8 @@ def test_genome_29x_every_pair_every_tile(X, orc, genome29, x):
     w = genome29.with_x(x)
     dev = X.DeviceInputs.from_workload(w)
     sc = X.scoring(1, -1, -1, x)
-    tiles = [(4, 16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16)]
+    tiles = [(4, 16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16),
+             (4, 8 | P16), (2, 16 | P16)]
     res = {}
     with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
         for t in tiles:
