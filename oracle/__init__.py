@@ -7,9 +7,13 @@ of ``bench.py`` may import this package; the CUDA library never does, and the
 two share no code.
 """
 from .oracle import (  # noqa: F401
+    NO_BEST,
+    ORC_PAIR,
+    ORC_RESULT,
+    align_pairs,
+    best_seeds,
     build,
     extend,
-    align_pairs,
-    unpack,
     load,
+    unpack,
 )

@@ -131,3 +131,40 @@ def align_pairs(packed, read_off, read_len, pairs, match=1, mismatch=-1,
     if with_cells:
         return out, cells[:n]
     return out
+
+
+NO_BEST = 0xFFFFFFFF
+
+
+def best_seeds(pairs, results, match=1):
+    """Several seeds per read pair, keeping the best extension.
+
+    Consecutive pair records with the same (a, b) (b with its strand flag)
+    are the seeds of one read pair, a group.  The total score of a record
+    is left_score + seed_len * match + right_score (seed-and-extend: the
+    exact seed scores seed_len matches; Section "Related works", BELLA
+    paragraph).  For every record p the result holds the index of the
+    record of p's group with the highest total score among records with
+    status 0; ties go to the lowest index; a group without such a record
+    gives NO_BEST.  Plain loops over the definition."""
+    pairs = np.asarray(pairs)
+    results = np.asarray(results)
+    n = len(pairs)
+    best = np.full(n, NO_BEST, np.uint32)
+    start = 0
+    while start < n:
+        end = start + 1
+        while (end < n and pairs["a"][end] == pairs["a"][start]
+               and pairs["b"][end] == pairs["b"][start]):
+            end += 1
+        winner, top = NO_BEST, None
+        for p in range(start, end):
+            if int(results["status"][p]) != 0:
+                continue
+            total = (int(results["left_score"][p]) + int(pairs["seed_len"][p]) * int(match)
+                     + int(results["right_score"][p]))
+            if top is None or total > top:
+                winner, top = p, total
+        best[start:end] = winner
+        start = end
+    return best

@@ -302,3 +302,22 @@ def test_x_monotonicity_is_reported_not_asserted(orc):
                 violations.append((a.tolist(), b.tolist(), x))
             prev = sc
     assert isinstance(violations, list)
+
+
+def test_best_seeds_hand_case(orc):
+    """Three seeds of read pair (0, 1), two of (0, 1) on the reverse strand,
+    one of (2, 3): totals 9, 12, 12 (tie: the lower index wins), 5 and an
+    invalid record, 7."""
+    pairs = np.zeros(6, W.PAIR_DTYPE)
+    for k, (a, b, L) in enumerate([(0, 1, 3), (0, 1, 4), (0, 1, 2), (0, 1 | W.PAIR_RC, 3),
+                                   (0, 1 | W.PAIR_RC, 3), (2, 3, 5)]):
+        pairs[k] = (a, b, 0, 0, L)
+    res = np.zeros(6, orc.ORC_RESULT)
+    for k, (ls, rs, st) in enumerate([(3, 3, 0), (4, 4, 0), (5, 5, 0), (1, 1, 0), (9, 9, 1),
+                                      (1, 1, 0)]):
+        res[k]["left_score"], res[k]["right_score"], res[k]["status"] = ls, rs, st
+    best = orc.best_seeds(pairs, res, match=1)
+    assert best.tolist() == [1, 1, 1, 3, 3, 5]
+    none = res.copy()
+    none["status"][5] = 1
+    assert orc.best_seeds(pairs, none, match=1)[5] == orc.NO_BEST
