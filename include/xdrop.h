@@ -231,6 +231,21 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
  * 16 bits run on the serving kernel's 32-bit second tier. */
 int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells);
 
+/* Several seeds per read pair, keeping the best extension.  Consecutive
+ * pair records with the same a and b (b with its strand flag) are the
+ * seeds of one read pair, a group.  For every record p, best[p] receives
+ * the index of the record of p's group with the highest total score
+ * left_score + seed_len * match + right_score among records with status
+ * XDROP_STATUS_OK; ties go to the lowest index; a group without such a
+ * record gives 0xFFFFFFFF.  pairs, results (as written by a submit) and
+ * best are device arrays of n entries (n < 2^31); the kernel runs
+ * asynchronously on the context's stream (xdrop_stream), after the work
+ * already queued there.  The exact seed scores seed_len matches (the
+ * seed-and-extend of Section "Related works", BELLA paragraph).
+ * XDROP_EINVAL for NULL arrays or too many records. */
+int xdrop_best_seeds_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_result *results,
+                            size_t n, int32_t match, uint32_t *best);
+
 /* Task ids (2*pair + 1 for a right extension, 2*pair for a left one)
  * that the first band tier handed to a wider tier during the most recently
  * synced ticket.  Copies up to cap ids to dst (host memory) and the total

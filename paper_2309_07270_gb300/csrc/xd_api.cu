@@ -980,6 +980,19 @@ int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st)
     return XDROP_OK;
 }
 
+int xdrop_best_seeds_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_result *results,
+                            size_t n, int32_t match, uint32_t *best)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    if (n == 0) return XDROP_OK;
+    if (!pairs || !results || !best) return fail(XDROP_EINVAL, "NULL array");
+    if ((uint64_t)n >= ((uint64_t)1 << 31)) return fail(XDROP_EINVAL, "too many records");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    CK(launch_best_seeds((const Pair *)pairs, (const int32_t *)results, n, match, best, c->stream));
+    return XDROP_OK;
+}
+
 int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells)
 {
     if (!c) return fail(XDROP_EINVAL, "context is NULL");

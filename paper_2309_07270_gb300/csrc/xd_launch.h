@@ -48,6 +48,9 @@ cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *
 cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *read_off,
                            const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s);
+// Best seed of every read pair (consecutive records with equal a, b).
+cudaError_t launch_best_seeds(const Pair *pairs, const int32_t *results, uint64_t n, int32_t match,
+                              uint32_t *best, cudaStream_t s);
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s);
 

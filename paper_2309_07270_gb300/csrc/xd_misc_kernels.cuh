@@ -135,4 +135,38 @@ __global__ void revcomp_kernel(const uint32_t *pk, int64_t n_words, const uint64
     }
 }
 
+// ---------------------------------------------------------------------------
+// Several seeds per read pair: consecutive records with the same a and b
+// form a group; the thread of a group's first record scans the group and
+// writes the index of its best valid record (highest left + seed_len*match
+// + right, lowest index on ties, 0xFFFFFFFF if none) for every member.
+// ---------------------------------------------------------------------------
+__global__ void best_seeds_kernel(const Pair *pairs, const int32_t *res, uint64_t n, int32_t match,
+                                  uint32_t *best)
+{
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const Pair q = pairs[p];
+        if (p > 0) {
+            const Pair r = pairs[p - 1];
+            if (r.a == q.a && r.b == q.b) continue;  // not the first record of its group
+        }
+        uint32_t win = 0xFFFFFFFFu;
+        int64_t top = 0;
+        uint64_t e = p;
+        for (; e < n; ++e) {
+            const Pair r = pairs[e];
+            if (e > p && (r.a != q.a || r.b != q.b)) break;
+            const int32_t *o = res + e * 7;
+            if (o[6] != 0) continue;
+            const int64_t tot = (int64_t)o[0] + (int64_t)r.seed_len * match + (int64_t)o[3];
+            if (win == 0xFFFFFFFFu || tot > top) {
+                win = (uint32_t)e;
+                top = tot;
+            }
+        }
+        for (uint64_t k = p; k < e; ++k) best[k] = win;
+    }
+}
+
 }  // namespace xd

@@ -71,6 +71,17 @@ cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *
     return cudaGetLastError();
 }
 
+cudaError_t launch_best_seeds(const Pair *pairs, const int32_t *results, uint64_t n, int32_t match,
+                              uint32_t *best, cudaStream_t s)
+{
+    if (!n) return cudaSuccess;
+    (void)cudaGetLastError();
+    const uint64_t blocks = (n + 255) / 256;
+    best_seeds_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(pairs, results, n,
+                                                                             match, best);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s)
 {

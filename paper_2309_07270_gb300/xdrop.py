@@ -41,7 +41,7 @@ EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_free", "xdrop_last_error", "xdrop_stream", "xdrop_get_stats",
            "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
            "xdrop_align_static", "xdrop_static_last_error", "xdrop_load_reads",
-           "xdrop_submit_pairs", "xdrop_get_serve_stats"]
+           "xdrop_submit_pairs", "xdrop_get_serve_stats", "xdrop_best_seeds_device"]
 
 
 class XdropError(RuntimeError):
@@ -102,11 +102,13 @@ def load():
                                              ctypes.POINTER(Scoring), vp]
     lib.xdrop_last_spills.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     lib.xdrop_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.xdrop_best_seeds_device.argtypes = [vp, vp, vp, sz, ctypes.c_int32, vp]
     lib.xdrop_load_reads.argtypes = [vp, vp, vp, vp, u32]
     lib.xdrop_submit_pairs.argtypes = [vp, vp, sz, ctypes.POINTER(Scoring), vp,
                                        ctypes.POINTER(u64)]
     lib.xdrop_get_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
-    for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats"):
+    for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats",
+                 "xdrop_best_seeds_device"):
         getattr(lib, name).restype = ctypes.c_int
     lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
                                        u32, vp, vp]
@@ -249,6 +251,11 @@ def xdrop_set_tile(ctx, lanes, cells):
     _check(load().xdrop_set_tile(ctx, int(lanes), int(cells)), ctx)
 
 
+def xdrop_best_seeds_device(ctx, pairs_ptr, results_ptr, n, match, best_ptr):
+    _check(load().xdrop_best_seeds_device(ctx, pairs_ptr, results_ptr, int(n), int(match),
+                                          best_ptr), ctx)
+
+
 def xdrop_last_spills(ctx, cap=1 << 24) -> np.ndarray:
     n = ctypes.c_size_t()
     buf = np.zeros(max(int(cap), 1), np.uint32)
@@ -295,6 +302,16 @@ class Aligner:
         t = self.submit_device(dev, sc)
         xdrop_sync(self.ctx, t)
         return dev.out
+
+    def best_seeds_device(self, dev, match):
+        """Best seed of every read pair of `dev` (see xdrop_best_seeds_device);
+        returns a uint32 torch tensor, one index per pair record."""
+        import torch
+        best = torch.zeros(max(dev.n_pairs, 1), dtype=torch.int32, device=dev.packed.device)
+        xdrop_best_seeds_device(self.ctx, dev.pairs.data_ptr(), dev.out.data_ptr(), dev.n_pairs,
+                                match, best.data_ptr())
+        torch.cuda.synchronize(dev.packed.device)
+        return best[: dev.n_pairs]
 
     def count_cells_device(self, dev, sc: Scoring):
         import torch

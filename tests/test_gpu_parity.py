@@ -4,6 +4,8 @@ Every field of every result (scores, coordinates, status) must be identical
 (integer work: bit-exact).  Cell counts from the library's counting pass
 must equal the oracle's.  Inputs are seeded synthetic workloads.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -328,3 +330,31 @@ def test_reverse_strand_resident_reads_and_device_submit(X, orc):
         res = dev.results()
     assert (res["status"][rcm] == X.XDROP_STATUS_INVALID).all()
     assert_same(res[~rcm], oracle_results(orc, w.subset(np.flatnonzero(~rcm))), "device forward")
+
+
+def test_best_seeds_device(X, orc):
+    """Several seeds per read pair: groups of 1-5 consecutive records with
+    the same reads, half of them at random (usually worse) seed positions;
+    the alignments and the device selection equal the oracle's."""
+    base = W.template_pairs(n_pairs=40, len_lo=600, len_hi=1500, seed=44)
+    rng = np.random.default_rng(45)
+    recs = []
+    for p in base.pairs:
+        la, lb = int(base.read_len[p["a"]]), int(base.read_len[p["b"]])
+        for _ in range(int(rng.integers(1, 6))):
+            q = p.copy()
+            if rng.random() < 0.5:  # another (random, usually worse) seed on the same reads
+                q["seed_a"] = rng.integers(0, la - 17)
+                q["seed_b"] = rng.integers(0, lb - 17)
+            recs.append(q)
+    w = base.subset(np.zeros(0, int))
+    w = dataclasses.replace(w, pairs=np.array(recs, dtype=base.pairs.dtype))
+    dev = X.DeviceInputs.from_workload(w)
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        al.align_device(dev, X.scoring(1, -1, -1, 50))
+        best = al.best_seeds_device(dev, 1).cpu().numpy().view(np.uint32)
+    res = dev.results()
+    assert_same(res, oracle_results(orc, w), "multi-seed alignments")
+    want = orc.best_seeds(w.pairs, res, match=1)
+    assert np.array_equal(best, want)
+    assert len(np.unique(want)) < len(want)  # groups of several seeds were reduced
