@@ -79,6 +79,18 @@ __host__ __device__ constexpr uint32_t idx2(int t)
     return (uint32_t)(2 * C2 - 1 - t) | ((uint32_t)(2 * C2 - 1 - (t + C2)) << 16);
 }
 
+// Lane slots of register t (low: t, high: t + C2) and their negations.
+template <int C2>
+__host__ __device__ constexpr uint32_t slot2(int t)
+{
+    return (uint32_t)t | ((uint32_t)(t + C2) << 16);
+}
+template <int C2>
+__host__ __device__ constexpr uint32_t nslot2(int t)
+{
+    return ((uint32_t)(-t) & 0xFFFFu) | (((uint32_t)(-(t + C2)) & 0xFFFFu) << 16);
+}
+
 template <int N>
 __device__ __forceinline__ uint32_t tree_max2(const uint32_t (&k)[N])
 {
@@ -106,8 +118,7 @@ __device__ __forceinline__ uint32_t tree_max2(const uint32_t (&k)[N])
 template <int C2, bool ODD, bool MASKED>
 __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
                                         uint32_t edge, uint32_t eq, uint32_t ma2, uint32_t mi2,
-                                        uint32_t nthr2, int32_t i0, int32_t j0, int32_t m,
-                                        int32_t n)
+                                        uint32_t nthr2, uint32_t lo1_2, uint32_t nhi1_2)
 {
     const uint32_t R[4] = {eq << 7, eq << 5, eq << 3, eq << 1};
     uint32_t key[C2];
@@ -121,8 +132,12 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
         const uint32_t s2 = (mk & ma2) | (~mk & mi2);
         uint32_t r = __viaddmax_s16x2(V[t], s2, nb);
         if (MASKED) {
-            if (i0 + t > m || j0 - t > n) r = (r & 0xFFFF0000u) | (kDead2 & 0xFFFFu);
-            if (i0 + t + C2 > m || j0 - t - C2 > n) r = (r & 0xFFFFu) | (kDead2 & 0xFFFF0000u);
+            // slot s lies in the rectangle iff lo <= s <= hi (lo = j0 - n,
+            // hi = m - i0): max(s - hi - 1, lo - 1 - s) < 0, per half
+            const uint32_t c = __viaddmax_s16x2(nslot2<C2>(t), lo1_2, 0x80008000u);
+            const uint32_t u = __viaddmax_s16x2(slot2<C2>(t), nhi1_2, c);
+            const uint32_t in = prmt(u, u, 0xBB99);  // 0xFFFF where inside
+            r = (r & in) | (kDead2 & ~in);
         }
         // 16*(r - thr) + (S-1-slot), floored at -16: negative iff pruned
         const uint32_t kc = __viaddmax_s16x2(idx2<C2>(t), nthr2, 0x80008000u);
@@ -219,6 +234,14 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             --lb_n;
         }
         const uint32_t nthr2 = pack2(-kScale * (T + Q));
+        // rectangle bounds of this lane's slots, clamped into 16 bits (only
+        // the masked copy reads them)
+        uint32_t lo1_2 = 0, nhi1_2 = 0;
+        if (MASKED) {
+            const int32_t lo = j0 - n, hi = m - i0;
+            lo1_2 = pack2(min(max(lo - 1, -1024), 1024));
+            nhi1_2 = pack2(min(max(-hi - 1, -1024), 1024));
+        }
         const uint32_t xx = Aw ^ Bw;
         const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
         int32_t lkey;
@@ -226,12 +249,12 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         if (ODD) {
             uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
             if (glane == L - 1) edge = kDead2;
-            lkey = dp16<C2, true, MASKED>(O, E, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            lkey = dp16<C2, true, MASKED>(O, E, edge, eq, ma2, mi2, nthr2, lo1_2, nhi1_2);
             vedge = __shfl_sync(FULL, O[C2 - 1], L - 1, L) >> 16;
         } else {
             uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
             if (glane == 0) edge = kDead2;
-            lkey = dp16<C2, false, MASKED>(E, O, edge, eq, ma2, mi2, nthr2, i0, j0, m, n);
+            lkey = dp16<C2, false, MASKED>(E, O, edge, eq, ma2, mi2, nthr2, lo1_2, nhi1_2);
             vedge = __shfl_sync(FULL, E[0], 0, L) & 0xFFFFu;
         }
         // Group key: value above lane above slot in lane, so one max finds

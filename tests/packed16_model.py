@@ -157,10 +157,17 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
                     s2 = (mk_ & ma2) | (~mk_ & mi2 & M32)
                     r = addmax2(V[g][t], s2, nb)
                     if masked:
-                        if i0[g] + t > m or j0[g] - t > n:
-                            r = (r & 0xFFFF0000) | (DEAD2 & 0xFFFF)
-                        if i0[g] + t + C2 > m or j0[g] - t - C2 > n:
-                            r = (r & 0xFFFF) | (DEAD2 & 0xFFFF0000)
+                        # slot s lies in the rectangle iff lo <= s <= hi:
+                        # max(s - hi - 1, lo - 1 - s) < 0, bounds clamped to 16 bits
+                        lo, hi = j0[g] - n, m - i0[g]
+                        lo1_2 = pack2(min(max(lo - 1, -1024), 1024))
+                        nhi1_2 = pack2(min(max(-hi - 1, -1024), 1024))
+                        slot2 = mk(t, t + C2)
+                        nslot2 = mk(-t, -(t + C2))
+                        c = addmax2(nslot2, lo1_2, 0x80008000)
+                        u = addmax2(slot2, nhi1_2, c)
+                        inside = prmt(u, u, 0xBB99)
+                        r = ((r & inside) | (DEAD2 & ~inside)) & M32
                     idx = (S - 1 - t) | ((S - 1 - (t + C2)) << 16)
                     kc = addmax2(idx, nthr2, 0x80008000)
                     key = addmax2(r, kc, 0xFFF0FFF0)
