@@ -10,7 +10,9 @@
  * paragraph: cells of one anti-diagonal are independent; Section
  * "Comparison between small dataset and large dataset": Needleman-Wunsch /
  * Smith-Waterman with X-drop).  The paper prints no recurrence; this
- * library computes the following reading exactly (bit-exact, int32):
+ * library computes the following reading exactly (bit-exact; int32 cells,
+ * or 16-bit cells in a normalised frame for scorings that fit them, with
+ * identical results):
  *
  *   Extension over a[1..m], b[1..n] (right: the bases after the seed;
  *   left: the bases before it, read backwards from the seed).  H(0,0) = 0;
@@ -20,7 +22,8 @@
  *   d = i+j is live iff R >= T_{d-1} - x; otherwise it is pruned.  The
  *   extension ends when two consecutive diagonals are entirely pruned or
  *   at d = m+n.  Its result is the final T and the first cell that reached
- *   it (smallest d, then smallest i).
+ *   it (smallest d, then smallest i).  A pair may name the reverse strand
+ *   of read b (XDROP_PAIR_RC below).
  *
  * Read layout (inputs).  2-bit codes A=0, C=1, G=2, T=3, 16 bases per
  * uint32 word, base k of the buffer in bits 2(k mod 16)..2(k mod 16)+1 of
@@ -63,7 +66,8 @@ extern "C" {
 
 /* xdrop_result.status values (per pair). */
 #define XDROP_STATUS_OK 0
-#define XDROP_STATUS_INVALID 1 /* device submit only: pair failed the limits */
+#define XDROP_STATUS_INVALID 1 /* device submit only: pair failed the limits
+                                  (or asks for the reverse strand there)     */
 #define XDROP_STATUS_TOO_LONG 2 /* xdrop_align_static: extension longer than its scratch */
 
 typedef struct xdrop_ctx xdrop_ctx;   /* opaque, owned by the library */
@@ -146,8 +150,10 @@ int xdrop_init(xdrop_ctx **out, int device, size_t device_mem_budget,
  * `out` (n_pairs results, host memory) belongs to the caller and must stay
  * valid until xdrop_sync(ticket) returns XDROP_OK; it is written during
  * that sync.  All pairs are validated first: any failure returns
- * XDROP_EINVAL and launches nothing.  n_pairs == 0 is valid (the ticket
- * completes at once).  Returns XDROP_OK and a ticket, or an error. */
+ * XDROP_EINVAL and launches nothing.  If any pair asks for the reverse
+ * strand (XDROP_PAIR_RC), the reverse complements of the reads are built
+ * on the device too (twice the packed size).  n_pairs == 0 is valid (the
+ * ticket completes at once).  Returns XDROP_OK and a ticket, or an error. */
 int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
                  const uint32_t *read_len, uint32_t n_reads,
                  const xdrop_pair *pairs, size_t n_pairs,
@@ -157,9 +163,11 @@ int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
  * device and stays owned by the caller; the arrays must stay valid and
  * unchanged until the ticket's sync returns.  n_words is the length of
  * `packed` in words.  Pairs are validated on the device: a pair that
- * fails the limits gets status XDROP_STATUS_INVALID and zero scores, the
- * others are aligned, and the ticket's sync returns XDROP_EINVAL.  Results
- * are written to `out` (device) by the time sync returns. */
+ * fails the limits (or asks for the reverse strand, XDROP_PAIR_RC, which
+ * needs the reverse complements only the host-side calls store) gets
+ * status XDROP_STATUS_INVALID and zero scores, the others are aligned,
+ * and the ticket's sync returns XDROP_EINVAL.  Results are written to
+ * `out` (device) by the time sync returns. */
 int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
                         const uint64_t *read_off, const uint32_t *read_len,
                         uint32_t n_reads, const xdrop_pair *pairs,
@@ -167,9 +175,11 @@ int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
                         xdrop_result *out, xdrop_ticket *t);
 
 /* Make a read set resident on the device for xdrop_submit_pairs (host
- * memory, same layout and limits as xdrop_submit; copied before return).
- * Replaces the previous read set; in serving mode it first waits for the
- * requests in flight.  Returns XDROP_OK, XDROP_EINVAL or XDROP_ECUDA. */
+ * memory, same layout and limits as xdrop_submit; copied before return,
+ * together with the reverse complement of every read for reverse-strand
+ * pairs: twice the packed size on the device).  Replaces the previous
+ * read set; in serving mode it first waits for the requests in flight.
+ * Returns XDROP_OK, XDROP_EINVAL or XDROP_ECUDA. */
 int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
                      const uint32_t *read_len, uint32_t n_reads);
 
@@ -177,9 +187,10 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
  * resident read set.  In batched mode with a device memory budget too small
  * for the whole pair table, the pairs stream through in chunks sized to the
  * budget, each one a replay of the same CUDA graph (xdrop_stats counts them
- * as graph_replays); XDROP_ENOMEM if not even a 1,024-pair chunk fits.  Results go to `out` (host memory, valid until the
- * ticket's sync returns XDROP_OK).  Pairs are validated first
- * (XDROP_EINVAL, nothing queued).
+ * as graph_replays); XDROP_ENOMEM if not even a 1,024-pair chunk fits.
+ * Results go to `out` (host memory, valid until the ticket's sync returns
+ * XDROP_OK).  Pairs are validated first (XDROP_EINVAL, nothing queued);
+ * reverse-strand pairs (XDROP_PAIR_RC) are accepted.
  *
  * Serving mode (XDROP_MODE_SERVE): thread-safe continuous batching.  The
  * request is queued, admitted once a slot is free and its device buffers
