@@ -34,7 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "X-drop GCUPS & pairs/s on 1 GB300 (bit-exact), batched vs plain; p99 @25 producers"
 UNIT = "GCUPS"
-INT_OPS_PER_CELL = 8  # algorithmic int32 ops per DP cell
+# algorithmic int ops per DP cell: 1 substitution select, 3 adds (diagonal + s,
+# up + gap, left + gap), 2 max, 1 threshold compare/select, 1 running max
+INT_OPS_PER_CELL = 8
 INT32_LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes, one warp instruction each per clock
 
 
