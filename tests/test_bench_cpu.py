@@ -1,0 +1,52 @@
+"""CPU checks of bench.py's bookkeeping (no GPU): the DRAM traffic of the
+roofline comes from profiles/traffic.txt only while the kernel sources it
+was measured on are unchanged."""
+import importlib.util
+import os
+import shutil
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def fake_tree(tmp_path):
+    csrc = tmp_path / "paper_2309_07270_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("xd_types.cuh", "xd_device.cuh", "xd_lockstep16.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_2309_07270_gb300", "csrc", f), csrc / f)
+    (tmp_path / "profiles").mkdir()
+    return csrc
+
+
+def test_traffic_is_used_only_for_the_measured_sources(tmp_path):
+    bench = load_bench()
+    csrc = fake_tree(tmp_path)
+    bench.ROOT = str(tmp_path)
+    sha = bench.kernel_source_sha()
+    assert len(sha) == 16
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        f"kernel=lockstep16_kernel<4,8> source_sha={sha} dram_bytes_per_launch=123\n"
+        f"kernel=lockstep16_kernel<8,8> source_sha=0000000000000000 dram_bytes_per_launch=456\n")
+    assert bench.traffic_from_profile("lockstep16_kernel<4,8>") == 123.0
+    assert bench.traffic_from_profile("lockstep16_kernel<8,8>") is None  # other sources
+    assert bench.traffic_from_profile("lockstep_kernel<4,16>") is None   # not measured
+    # any change to the kernel sources drops the number
+    with open(csrc / "xd_lockstep16.cuh", "a") as f:
+        f.write("\n")
+    assert bench.kernel_source_sha() != sha
+    assert bench.traffic_from_profile("lockstep16_kernel<4,8>") is None
+
+
+def test_committed_traffic_file_parses():
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        assert f["kernel"].startswith("lockstep")
+        assert len(f["source_sha"]) == 16
+        assert float(f["dram_bytes_per_launch"]) > 0
