@@ -257,6 +257,42 @@ int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells);
 int xdrop_best_seeds_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_result *results,
                             size_t n, int32_t match, uint32_t *best);
 
+/* Seed discovery: the candidate pairs of the resident read set
+ * (xdrop_load_reads), the step upstream of seed-and-extend (Section
+ * "Related works", diBELLA 2D paragraph: overlaps are the nonzeros of
+ * A * A^T, A the read-by-reliable-k-mer matrix; Section "Experimental
+ * Setup": k = 31, stride 1, frequency window [20, 30] or [20, 50]).
+ *
+ * A k-mer is k consecutive bases of a read starting at a multiple of
+ * stride; its canonical code is the smaller 2k-bit code (first base most
+ * significant) of the k-mer and of its reverse complement.  Its count is
+ * its number of occurrences in all reads (repeats in one read included);
+ * it is reliable iff lo <= count <= hi.  Reads a < b are a candidate pair
+ * iff they share a reliable k-mer (its first occurrence in each read
+ * counts).  The pair's seed is the shared k-mer with the smallest position
+ * in a (then in b, then the smallest code): seed_a and seed_b are its
+ * first positions, seed_len = k; if it was read on opposite strands of a
+ * and b, b carries XDROP_PAIR_RC and seed_b = len_b - k - pos_b, a
+ * position in b's reverse complement.  The records can be passed as they
+ * are to xdrop_submit_pairs.
+ *
+ * Writes min(cap, total) candidates in increasing (a, b) order to pairs
+ * and, unless shared is NULL, the number of shared reliable k-mers of each
+ * to shared (host memory); *n = total.  The result stays in the context
+ * until the read set or the parameters change, so a call with a larger cap
+ * only copies.  Synchronous.  Limits: 1 <= k <= 32, stride >= 1,
+ * 1 <= lo <= hi <= 1024 (XDROP_EINVAL; also without resident reads);
+ * fewer than 2^31 occurrences and 2^31 (pair, shared k-mer) entries, and
+ * the context's memory budget (XDROP_ENOMEM). */
+typedef struct {
+    uint32_t k;      /* k-mer length                               */
+    uint32_t stride; /* a k-mer starts at every stride-th position */
+    uint32_t lo, hi; /* reliable iff lo <= count <= hi             */
+} xdrop_kmer_params;
+
+int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *pairs,
+                          uint32_t *shared, size_t cap, size_t *n);
+
 /* Task ids (2*pair + 1 for a right extension, 2*pair for a left one)
  * that the first band tier handed to a wider tier during the most recently
  * synced ticket.  Copies up to cap ids to dst (host memory) and the total

@@ -139,7 +139,14 @@ struct xdrop_ctx {
     uint64_t r_words = 0;
     uint32_t r_n = 0, r_maxlen = 0;
     bool have_reads = false;
+    uint64_t reads_gen = 0;  // bumped by every xdrop_load_reads
     xd::Server *srv = nullptr;
+
+    // the last seed discovery result (xdrop_find_candidates)
+    std::vector<Pair> cand_pairs;
+    std::vector<uint32_t> cand_shared;
+    std::tuple<uint32_t, uint32_t, uint32_t, uint32_t> cand_params;
+    uint64_t cand_gen = 0;  // reads_gen it was computed on; 0: none
 };
 
 constexpr uint64_t kServeTicket = 1ull << 63;
@@ -811,6 +818,7 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
     c->r_n = n_reads;
     c->r_maxlen = maxlen;
     c->have_reads = true;
+    ++c->reads_gen;
     if ((rc = ensure_scratch(c, 0, maxlen))) return rc;
     if (c->mode == XDROP_MODE_SERVE) {
         xd::ResidentReads rr;
@@ -977,6 +985,39 @@ int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st)
         st->spill_taken = s.spill_taken;
         st->ring_warps = s.ring_warps;
     }
+    return XDROP_OK;
+}
+
+int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *pairs,
+                          uint32_t *shared, size_t cap, size_t *n)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    if (!p || !n || (cap && !pairs)) return fail(XDROP_EINVAL, "NULL argument");
+    if (p->k < 1 || p->k > 32 || p->stride < 1 || p->lo < 1 || p->lo > p->hi || p->hi > 1024)
+        return fail(XDROP_EINVAL, "k-mer parameters out of range (k %u, stride %u, lo %u, hi %u)",
+                    p->k, p->stride, p->lo, p->hi);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->have_reads) return fail(XDROP_EINVAL, "no resident reads (xdrop_load_reads)");
+    CK(cudaSetDevice(c->device));
+    const auto key = std::make_tuple(p->k, p->stride, p->lo, p->hi);
+    if (c->cand_gen != c->reads_gen || c->cand_params != key) {
+        c->cand_gen = 0;
+        const size_t left = c->budget ? (c->budget > c->used ? c->budget - c->used : 1) : 0;
+        std::string err;
+        const int rc = find_candidates(c->stream, c->sm_count, left, (const uint32_t *)c->r_packed.p,
+                                       (const uint64_t *)c->r_off.p, (const uint32_t *)c->r_len.p,
+                                       c->r_n, c->h_len.data(), p->k, p->stride, p->lo, p->hi,
+                                       c->cand_pairs, c->cand_shared, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+        c->cand_params = key;
+        c->cand_gen = c->reads_gen;
+    }
+    const size_t total = c->cand_pairs.size(), m = std::min(cap, total);
+    if (m) {
+        memcpy(pairs, c->cand_pairs.data(), m * sizeof(xdrop_pair));
+        if (shared) memcpy(shared, c->cand_shared.data(), m * sizeof(uint32_t));
+    }
+    *n = total;
     return XDROP_OK;
 }
 

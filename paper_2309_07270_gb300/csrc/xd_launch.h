@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 #include "xd_types.cuh"
 
 namespace xd {
@@ -51,6 +54,14 @@ cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *
 // Best seed of every read pair (consecutive records with equal a, b).
 cudaError_t launch_best_seeds(const Pair *pairs, const int32_t *results, uint64_t n, int32_t match,
                               uint32_t *best, cudaStream_t s);
+// Seed discovery over a read set on the device (xd_seeds.cu): the candidate
+// pairs and their shared-k-mer counts, in (a, b) order, into host vectors.
+// Synchronous on `s`.  Returns an XDROP_* code, with a message in err.
+int find_candidates(cudaStream_t s, int sm_count, size_t budget, const uint32_t *packed,
+                    const uint64_t *read_off, const uint32_t *read_len, uint32_t n_reads,
+                    const uint32_t *h_len, uint32_t k, uint32_t stride, uint32_t lo, uint32_t hi,
+                    std::vector<Pair> &out_pairs, std::vector<uint32_t> &out_shared,
+                    std::string &err);
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s);
 

@@ -113,8 +113,9 @@ def pack_reads(reads) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
 
 
 def mutate(template: np.ndarray, rng: np.random.Generator,
-           protect: np.ndarray | None = None):
-    """Apply the error model to ``template`` (codes).
+           protect: np.ndarray | None = None, rates=None):
+    """Apply the error model to ``template`` (codes); ``rates`` =
+    (substitution, deletion, insertion) replaces the default 4% each.
 
     Returns (read, counts, sub, dele, ins): the erroneous copy, the number of
     read bases each template base emitted (0, 1 or 2), and the per-template
@@ -128,10 +129,11 @@ def mutate(template: np.ndarray, rng: np.random.Generator,
         n = t.shape[0]
         if n == 0:
             break
+        p_sub, p_del, p_ins = rates if rates is not None else (P_SUB, P_DEL, P_INS)
         u = rng.random(n, dtype=np.float32)
-        sub = u < P_SUB
-        dele = (u >= P_SUB) & (u < P_SUB + P_DEL)
-        ins = (u >= P_SUB + P_DEL) & (u < P_SUB + P_DEL + P_INS)
+        sub = u < p_sub
+        dele = (u >= p_sub) & (u < p_sub + p_del)
+        ins = (u >= p_sub + p_del) & (u < p_sub + p_del + p_ins)
         if protect is not None:
             keep = ~protect[c0:c0 + n]
             sub &= keep
@@ -285,6 +287,29 @@ def genome_overlaps(genome_len=4_600_000, coverage=29.0, mean_len=10_000,
                     dict(seed=seed, genome_len=G, coverage=coverage,
                          n_reads=n_reads, dropped=int((~keep).sum()),
                          mean_len=mean_len, sd_len=sd_len))
+
+
+def sequencing_reads(genome_len=200_000, coverage=29.0, mean_len=10_000, sd_len=6_000,
+                     min_len=1_000, rc_frac=0.5, seed=11, error_rate=None):
+    """Reads of one uniform random genome under the error model (or, with
+    ``error_rate``, substitutions, deletions and insertions at a third of it
+    each), each one stored as its reverse complement with probability
+    ``rc_frac`` (reads come from both strands): the input of seed discovery.
+    Lengths are lognormal as in genome_overlaps.  Returns (packed,
+    read_off, read_len)."""
+    rates = None if error_rate is None else (error_rate / 3,) * 3
+    rng = np.random.Generator(np.random.PCG64(seed))
+    G = int(genome_len)
+    genome = rng.integers(0, 4, size=G, dtype=np.uint8)
+    n_reads = max(int(math.ceil(coverage * G / mean_len)), 1)
+    lens = _lognormal_lengths(rng, n_reads, mean_len, sd_len, min(min_len, G), G)
+    starts = rng.integers(0, G - lens + 1, dtype=np.int64)
+    flip = rng.random(n_reads) < rc_frac
+    reads = []
+    for r in range(n_reads):
+        rd = mutate(genome[starts[r]:starts[r] + lens[r]], rng, rates=rates)[0]
+        reads.append(revcomp(rd) if flip[r] else rd)
+    return pack_reads(reads)
 
 
 def _choose_seeds(pa, pb, starts, ends, oks, radius=1024):

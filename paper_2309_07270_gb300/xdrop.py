@@ -41,7 +41,8 @@ EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_free", "xdrop_last_error", "xdrop_stream", "xdrop_get_stats",
            "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
            "xdrop_align_static", "xdrop_static_last_error", "xdrop_load_reads",
-           "xdrop_submit_pairs", "xdrop_get_serve_stats", "xdrop_best_seeds_device"]
+           "xdrop_submit_pairs", "xdrop_get_serve_stats", "xdrop_best_seeds_device",
+           "xdrop_find_candidates"]
 
 
 class XdropError(RuntimeError):
@@ -70,6 +71,11 @@ class ServeStats(ctypes.Structure):
                 ("admission_waits", ctypes.c_uint64), ("published", ctypes.c_uint64),
                 ("consumed", ctypes.c_uint64), ("spill_reserved", ctypes.c_uint64),
                 ("spill_taken", ctypes.c_uint64), ("ring_warps", ctypes.c_uint64)]
+
+
+class KmerParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("stride", ctypes.c_uint32),
+                ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32)]
 
 
 _lib = None
@@ -107,8 +113,10 @@ def load():
     lib.xdrop_submit_pairs.argtypes = [vp, vp, sz, ctypes.POINTER(Scoring), vp,
                                        ctypes.POINTER(u64)]
     lib.xdrop_get_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    lib.xdrop_find_candidates.argtypes = [vp, ctypes.POINTER(KmerParams), vp, vp, sz,
+                                          ctypes.POINTER(sz)]
     for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats",
-                 "xdrop_best_seeds_device"):
+                 "xdrop_best_seeds_device", "xdrop_find_candidates"):
         getattr(lib, name).restype = ctypes.c_int
     lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
                                        u32, vp, vp]
@@ -256,6 +264,21 @@ def xdrop_best_seeds_device(ctx, pairs_ptr, results_ptr, n, match, best_ptr):
                                           best_ptr), ctx)
 
 
+def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1):
+    """Candidate pairs of the resident reads (pairs as PAIR_DTYPE, ready for
+    xdrop_submit_pairs) and their shared reliable k-mer counts."""
+    prm = KmerParams(int(k), int(stride), int(lo), int(hi))
+    n = ctypes.c_size_t()
+    _check(load().xdrop_find_candidates(ctx, ctypes.byref(prm), None, None, 0, ctypes.byref(n)),
+           ctx)
+    pairs = np.zeros(n.value, PAIR_DTYPE)
+    shared = np.zeros(n.value, np.uint32)
+    if n.value:  # the context kept the result: this call only copies it
+        _check(load().xdrop_find_candidates(ctx, ctypes.byref(prm), _p(pairs), _p(shared),
+                                            n.value, ctypes.byref(n)), ctx)
+    return pairs, shared
+
+
 def xdrop_last_spills(ctx, cap=1 << 24) -> np.ndarray:
     n = ctypes.c_size_t()
     buf = np.zeros(max(int(cap), 1), np.uint32)
@@ -312,6 +335,12 @@ class Aligner:
                                 match, best.data_ptr())
         torch.cuda.synchronize(dev.packed.device)
         return best[: dev.n_pairs]
+
+    def find_candidates(self, packed, read_off, read_len, k=31, lo=20, hi=30, stride=1):
+        """Load a read set and return its candidate pairs and shared counts
+        (xdrop_find_candidates); the reads stay resident for submit_pairs."""
+        xdrop_load_reads(self.ctx, packed, read_off, read_len)
+        return xdrop_find_candidates(self.ctx, k, lo, hi, stride)
 
     def count_cells_device(self, dev, sc: Scoring):
         import torch
