@@ -78,3 +78,28 @@ def test_candidates_are_the_nonzeros_of_a_times_a_transpose():
     cands = S.candidate_pairs(packed, off, lens, k=15, lo=2, hi=6)
     got = {(int(c["a"]), int(c["b"]) & 0x7FFFFFFF): int(c["shared"]) for c in cands}
     assert got == want
+
+
+def test_seed_position_in_a_decides_alone():
+    """A position of read a holds one k-mer, so the shared k-mers of a pair
+    have distinct first positions in a: the smallest one picks the seed and
+    the later tie-breaks (position in b, code) never decide.  Checked by
+    brute force over every candidate pair."""
+    reads = overlap_set()
+    codes = [r.tolist() for r in reads]
+    keep = S.reliable_kmers(codes, 15, 2, 6)
+    first = {}
+    for code, r, p, _ in S.occurrences(codes, 15):
+        if code in keep:
+            first.setdefault((r, code), p)
+    by_read = {}
+    for (r, code), p in first.items():
+        by_read.setdefault(r, {})[code] = p
+    packed, off, lens = pack(reads)
+    cands = S.candidate_pairs(packed, off, lens, k=15, lo=2, hi=6)
+    for c in cands:
+        a, b = int(c["a"]), int(c["b"]) & 0x7FFFFFFF
+        shared = set(by_read[a]) & set(by_read[b])
+        pos_a = [by_read[a][m] for m in shared]
+        assert len(pos_a) == len(set(pos_a)) == c["shared"]
+        assert min(pos_a) == c["seed_a"]
