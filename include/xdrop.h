@@ -283,15 +283,41 @@ int xdrop_best_seeds_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_r
  * only copies.  Synchronous.  Limits: 1 <= k <= 32, stride >= 1,
  * 1 <= lo <= hi <= 1024 (XDROP_EINVAL; also without resident reads);
  * fewer than 2^31 occurrences and 2^31 (pair, shared k-mer) entries, and
- * the context's memory budget (XDROP_ENOMEM). */
+ * the context's memory budget (XDROP_ENOMEM).
+ *
+ * Two products compute the same candidates.  XDROP_SEEDS_SORT (default)
+ * writes one entry per (read pair, shared reliable k-mer), sorts the
+ * entries by pair and reduces them.  XDROP_SEEDS_ROWWISE builds A's rows
+ * and columns and accumulates each read's partners in a shared-memory hash
+ * table of 2,048 slots, one thread block per read, without per-entry
+ * tables; a read with more partners than that makes the call run the
+ * sort-based product instead.  xdrop_get_seed_stats tells which ran. */
+#define XDROP_SEEDS_SORT 0u
+#define XDROP_SEEDS_ROWWISE 1u
+
 typedef struct {
     uint32_t k;      /* k-mer length                               */
     uint32_t stride; /* a k-mer starts at every stride-th position */
     uint32_t lo, hi; /* reliable iff lo <= count <= hi             */
+    uint32_t flags;  /* XDROP_SEEDS_SORT or XDROP_SEEDS_ROWWISE    */
 } xdrop_kmer_params;
 
 int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *pairs,
                           uint32_t *shared, size_t cap, size_t *n);
+
+/* Counters of the last xdrop_find_candidates that computed (not of calls
+ * that only copied a kept result). */
+typedef struct {
+    double ms;            /* device time, CUDA events around the pipeline  */
+    uint64_t occurrences; /* k-mer occurrences                             */
+    uint64_t runs;        /* k-mers that occur at least twice              */
+    uint64_t candidates;  /* candidate pairs                               */
+    uint32_t product;     /* XDROP_SEEDS_SORT or XDROP_SEEDS_ROWWISE: the
+                             product that produced them                    */
+    uint32_t pad;
+} xdrop_seed_stats;
+
+int xdrop_get_seed_stats(xdrop_ctx *c, xdrop_seed_stats *st);
 
 /* Task ids (2*pair + 1 for a right extension, 2*pair for a left one)
  * that the first band tier handed to a wider tier during the most recently

@@ -145,8 +145,9 @@ struct xdrop_ctx {
     // the last seed discovery result (xdrop_find_candidates)
     std::vector<Pair> cand_pairs;
     std::vector<uint32_t> cand_shared;
-    std::tuple<uint32_t, uint32_t, uint32_t, uint32_t> cand_params;
+    std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, uint32_t> cand_params;
     uint64_t cand_gen = 0;  // reads_gen it was computed on; 0: none
+    xd::SeedStats seed_stats;
 };
 
 constexpr uint64_t kServeTicket = 1ull << 63;
@@ -993,13 +994,15 @@ int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *
 {
     if (!c) return fail(XDROP_EINVAL, "context is NULL");
     if (!p || !n || (cap && !pairs)) return fail(XDROP_EINVAL, "NULL argument");
-    if (p->k < 1 || p->k > 32 || p->stride < 1 || p->lo < 1 || p->lo > p->hi || p->hi > 1024)
-        return fail(XDROP_EINVAL, "k-mer parameters out of range (k %u, stride %u, lo %u, hi %u)",
-                    p->k, p->stride, p->lo, p->hi);
+    if (p->k < 1 || p->k > 32 || p->stride < 1 || p->lo < 1 || p->lo > p->hi || p->hi > 1024 ||
+        (p->flags & ~XDROP_SEEDS_ROWWISE))
+        return fail(XDROP_EINVAL,
+                    "k-mer parameters out of range (k %u, stride %u, lo %u, hi %u, flags %u)", p->k,
+                    p->stride, p->lo, p->hi, p->flags);
     std::lock_guard<std::mutex> lk(c->mu);
     if (!c->have_reads) return fail(XDROP_EINVAL, "no resident reads (xdrop_load_reads)");
     CK(cudaSetDevice(c->device));
-    const auto key = std::make_tuple(p->k, p->stride, p->lo, p->hi);
+    const auto key = std::make_tuple(p->k, p->stride, p->lo, p->hi, p->flags);
     if (c->cand_gen != c->reads_gen || c->cand_params != key) {
         c->cand_gen = 0;
         const size_t left = c->budget ? (c->budget > c->used ? c->budget - c->used : 1) : 0;
@@ -1007,7 +1010,8 @@ int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *
         const int rc = find_candidates(c->stream, c->sm_count, left, (const uint32_t *)c->r_packed.p,
                                        (const uint64_t *)c->r_off.p, (const uint32_t *)c->r_len.p,
                                        c->r_n, c->h_len.data(), p->k, p->stride, p->lo, p->hi,
-                                       c->cand_pairs, c->cand_shared, err);
+                                       p->flags, c->cand_pairs, c->cand_shared, c->seed_stats,
+                                       err);
         if (rc) return fail(rc, "%s", err.c_str());
         c->cand_params = key;
         c->cand_gen = c->reads_gen;
@@ -1018,6 +1022,19 @@ int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *
         if (shared) memcpy(shared, c->cand_shared.data(), m * sizeof(uint32_t));
     }
     *n = total;
+    return XDROP_OK;
+}
+
+int xdrop_get_seed_stats(xdrop_ctx *c, xdrop_seed_stats *st)
+{
+    if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    memset(st, 0, sizeof *st);
+    st->ms = c->seed_stats.ms;
+    st->occurrences = c->seed_stats.occurrences;
+    st->runs = c->seed_stats.runs;
+    st->candidates = c->seed_stats.candidates;
+    st->product = c->seed_stats.product;
     return XDROP_OK;
 }
 

@@ -56,12 +56,20 @@ cudaError_t launch_best_seeds(const Pair *pairs, const int32_t *results, uint64_
                               uint32_t *best, cudaStream_t s);
 // Seed discovery over a read set on the device (xd_seeds.cu): the candidate
 // pairs and their shared-k-mer counts, in (a, b) order, into host vectors.
-// Synchronous on `s`.  Returns an XDROP_* code, with a message in err.
+// flags: XDROP_SEEDS_ROWWISE selects the row-wise product.  Synchronous on
+// `s`.  Returns an XDROP_* code, with a message in err.
+struct SeedStats {
+    double ms = 0;              // CUDA events, first kernel to the last copy
+    uint64_t occurrences = 0;   // k-mer occurrences
+    uint64_t runs = 0;          // k-mers seen at least twice
+    uint64_t candidates = 0;
+    uint32_t product = 0;       // XDROP_SEEDS_SORT or XDROP_SEEDS_ROWWISE: the one that ran
+};
 int find_candidates(cudaStream_t s, int sm_count, size_t budget, const uint32_t *packed,
                     const uint64_t *read_off, const uint32_t *read_len, uint32_t n_reads,
                     const uint32_t *h_len, uint32_t k, uint32_t stride, uint32_t lo, uint32_t hi,
-                    std::vector<Pair> &out_pairs, std::vector<uint32_t> &out_shared,
-                    std::string &err);
+                    uint32_t flags, std::vector<Pair> &out_pairs,
+                    std::vector<uint32_t> &out_shared, SeedStats &stats, std::string &err);
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s);
 

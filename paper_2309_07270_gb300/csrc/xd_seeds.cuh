@@ -181,6 +181,105 @@ struct CandMerge {
     }
 };
 
+// Distinct reads of a run (the nonzeros of its column of A), 0 for a run
+// outside [lo, hi].
+XS_HD uint32_t run_reads(const uint32_t *occ, const uint32_t *occ_rd, uint64_t s, uint32_t cnt,
+                         uint32_t lo, uint32_t hi)
+{
+    if (cnt < lo || cnt > hi) return 0;
+    uint32_t u = 0;
+    for (uint32_t i = 0; i < cnt; ++i) u += first_in_read(occ, occ_rd, s, i);
+    return u;
+}
+
+// ---------------------------------------------------------------------------
+// Row-wise product (Gustavson): read a's candidates are accumulated over its
+// reliable k-mers (row a of A) and, for each, the other reads holding it
+// (the k-mer's column).  Columns hold member words (read << 32) |
+// (position << 1) | forward, in read order; rows hold (column, position << 1 |
+// forward).  Per partner b > a the accumulator keeps the number of shared
+// k-mers and the minimum of seed_key: the position in a decides alone (a
+// position of a holds one k-mer, so the shared k-mers' positions in a are
+// distinct), then seed_b and the strand ride along.
+
+XS_HD uint64_t member_word(uint32_t read, uint32_t pos, bool fwd)
+{
+    return ((uint64_t)read << 32) | ((uint64_t)pos << 1) | (fwd ? 1u : 0u);
+}
+
+XS_HD uint64_t seed_key(uint32_t pa, uint32_t sb, bool rc)
+{
+    return ((uint64_t)pa << 32) | ((uint64_t)sb << 1) | (rc ? 1u : 0u);
+}
+
+// Column entries of a reliable run: its reads' first occurrences, in order.
+XS_HD void run_members(const uint32_t *occ, const uint32_t *occ_rd, const uint32_t *fwd_bits,
+                       const uint64_t *occ_off, uint64_t s, uint32_t cnt, uint32_t stride,
+                       uint64_t *out)
+{
+    uint32_t j = 0;
+    for (uint32_t i = 0; i < cnt; ++i) {
+        if (!first_in_read(occ, occ_rd, s, i)) continue;
+        const uint32_t q = occ[s + i], r = occ_rd[q];
+        out[j++] = member_word(r, (uint32_t)((q - occ_off[r]) * stride), fwd_bit(fwd_bits, q));
+    }
+}
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kTableLg = 11;  // 2,048 partners per read in shared memory
+constexpr uint32_t kOverflow = 0xFFFFFFFFu;
+
+struct RowTable {
+    uint32_t *key;            // partner read id, kEmpty when free
+    uint32_t *cnt;            // shared k-mers
+    unsigned long long *best; // minimum seed_key
+    uint32_t lg;              // 2^lg slots
+};
+
+XS_HD uint32_t table_slot(uint32_t b, uint32_t lg)
+{
+    return (b * 2654435761u) >> (32 - lg);  // multiplicative hash, top bits
+}
+
+// Adds one shared k-mer of partner b; false when the table is full.  On
+// the device the slots are claimed and updated with shared-memory atomics
+// (insertions from all threads of the block at once); on the host in order.
+XS_HD bool table_add(const RowTable &t, uint32_t b, uint64_t key)
+{
+    const uint32_t mask = (1u << t.lg) - 1;
+    uint32_t h = table_slot(b, t.lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+#if defined(__CUDA_ARCH__)
+        const uint32_t prev = atomicCAS(&t.key[h], kEmpty, b);
+#else
+        const uint32_t prev = t.key[h];
+        if (prev == kEmpty) t.key[h] = b;
+#endif
+        if (prev != kEmpty && prev != b) continue;
+#if defined(__CUDA_ARCH__)
+        atomicAdd(&t.cnt[h], 1u);
+        atomicMin(&t.best[h], (unsigned long long)key);
+#else
+        t.cnt[h] += 1;
+        if (key < t.best[h]) t.best[h] = key;
+#endif
+        return true;
+    }
+    return false;
+}
+
+// One (row entry, column member) product term of read a: a k-mer at
+// position pa of a (forward fa) that read member>>32 also holds.
+XS_HD bool row_term(const RowTable &t, uint32_t a, uint32_t pa, bool fa, uint64_t member,
+                    const uint32_t *read_len, uint32_t k)
+{
+    const uint32_t b = (uint32_t)(member >> 32);
+    if (b <= a) return true;
+    const uint32_t pb = (uint32_t)(member & 0xFFFFFFFFu) >> 1;
+    const bool rc = fa != ((member & 1u) != 0);
+    return table_add(t, b, seed_key(pa, rc ? read_len[b] - k - pb : pb, rc));
+}
+
 // Bits per read id in a pair key: the smallest nb >= 1 with n_reads <= 2^nb.
 inline uint32_t id_bits(uint32_t n_reads)
 {

@@ -24,6 +24,8 @@ XDROP_EBUSY = -5
 XDROP_MODE_BATCHED = 0
 XDROP_MODE_PLAIN = 1
 XDROP_MODE_SERVE = 2
+XDROP_SEEDS_SORT = 0
+XDROP_SEEDS_ROWWISE = 1
 XDROP_STATUS_OK = 0
 XDROP_STATUS_INVALID = 1
 XDROP_STATUS_TOO_LONG = 2
@@ -42,7 +44,7 @@ EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
            "xdrop_align_static", "xdrop_static_last_error", "xdrop_load_reads",
            "xdrop_submit_pairs", "xdrop_get_serve_stats", "xdrop_best_seeds_device",
-           "xdrop_find_candidates"]
+           "xdrop_find_candidates", "xdrop_get_seed_stats"]
 
 
 class XdropError(RuntimeError):
@@ -75,7 +77,13 @@ class ServeStats(ctypes.Structure):
 
 class KmerParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_uint32), ("stride", ctypes.c_uint32),
-                ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32)]
+                ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class SeedStats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("occurrences", ctypes.c_uint64),
+                ("runs", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("product", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 _lib = None
@@ -115,8 +123,9 @@ def load():
     lib.xdrop_get_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
     lib.xdrop_find_candidates.argtypes = [vp, ctypes.POINTER(KmerParams), vp, vp, sz,
                                           ctypes.POINTER(sz)]
+    lib.xdrop_get_seed_stats.argtypes = [vp, ctypes.POINTER(SeedStats)]
     for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats",
-                 "xdrop_best_seeds_device", "xdrop_find_candidates"):
+                 "xdrop_best_seeds_device", "xdrop_find_candidates", "xdrop_get_seed_stats"):
         getattr(lib, name).restype = ctypes.c_int
     lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
                                        u32, vp, vp]
@@ -264,10 +273,12 @@ def xdrop_best_seeds_device(ctx, pairs_ptr, results_ptr, n, match, best_ptr):
                                           best_ptr), ctx)
 
 
-def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1):
+def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1, rowwise=False):
     """Candidate pairs of the resident reads (pairs as PAIR_DTYPE, ready for
-    xdrop_submit_pairs) and their shared reliable k-mer counts."""
-    prm = KmerParams(int(k), int(stride), int(lo), int(hi))
+    xdrop_submit_pairs) and their shared reliable k-mer counts; ``rowwise``
+    selects the row-wise product (same result)."""
+    prm = KmerParams(int(k), int(stride), int(lo), int(hi),
+                     XDROP_SEEDS_ROWWISE if rowwise else XDROP_SEEDS_SORT)
     n = ctypes.c_size_t()
     _check(load().xdrop_find_candidates(ctx, ctypes.byref(prm), None, None, 0, ctypes.byref(n)),
            ctx)
@@ -277,6 +288,12 @@ def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1):
         _check(load().xdrop_find_candidates(ctx, ctypes.byref(prm), _p(pairs), _p(shared),
                                             n.value, ctypes.byref(n)), ctx)
     return pairs, shared
+
+
+def xdrop_get_seed_stats(ctx) -> dict:
+    st = SeedStats()
+    _check(load().xdrop_get_seed_stats(ctx, ctypes.byref(st)), ctx)
+    return {k: getattr(st, k) for k, _ in SeedStats._fields_ if k != "pad"}
 
 
 def xdrop_last_spills(ctx, cap=1 << 24) -> np.ndarray:
@@ -336,11 +353,12 @@ class Aligner:
         torch.cuda.synchronize(dev.packed.device)
         return best[: dev.n_pairs]
 
-    def find_candidates(self, packed, read_off, read_len, k=31, lo=20, hi=30, stride=1):
+    def find_candidates(self, packed, read_off, read_len, k=31, lo=20, hi=30, stride=1,
+                        rowwise=False):
         """Load a read set and return its candidate pairs and shared counts
         (xdrop_find_candidates); the reads stay resident for submit_pairs."""
         xdrop_load_reads(self.ctx, packed, read_off, read_len)
-        return xdrop_find_candidates(self.ctx, k, lo, hi, stride)
+        return xdrop_find_candidates(self.ctx, k, lo, hi, stride, rowwise)
 
     def count_cells_device(self, dev, sc: Scoring):
         import torch

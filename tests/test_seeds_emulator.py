@@ -1,6 +1,7 @@
 """Seed discovery's per-element steps (csrc/xd_seeds.cuh), run on the CPU in
-the device pipeline's order by tests/seeds_emulator.cpp, against the oracle
-(oracle/seeds.py) record for record: k from 1 to 32 (windows over one, two
+the device pipeline's order by tests/seeds_emulator.cpp for both products
+(sort-based and row-wise), against the oracle (oracle/seeds.py) record for
+record: k from 1 to 32 (windows over one, two
 and three packed words), strides, repeats inside a read, reads shorter
 than k, empty reads, read counts around the key-width boundaries."""
 import ctypes
@@ -18,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
-def emu(tmp_path_factory):
+def lib(tmp_path_factory):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("no g++")
@@ -26,20 +27,39 @@ def emu(tmp_path_factory):
     subprocess.run([gxx, "-O2", "-std=c++17", "-Wall", "-Werror", "-shared", "-fPIC", "-o", str(so),
                     os.path.join(HERE, "seeds_emulator.cpp")], check=True)
     lib = ctypes.CDLL(str(so))
-    vp, u32 = ctypes.c_void_p, ctypes.c_uint32
-    lib.emulate_candidates.restype = ctypes.c_int64
-    lib.emulate_candidates.argtypes = [vp, vp, vp, u32, u32, u32, u32, u32, vp, ctypes.c_int64]
+    vp, u32, i64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int64
+    lib.emulate_candidates.restype = i64
+    lib.emulate_candidates.argtypes = [vp, vp, vp, u32, u32, u32, u32, u32, vp, i64]
+    lib.emulate_candidates_rowwise.restype = i64
+    lib.emulate_candidates_rowwise.argtypes = [vp, vp, vp, u32, u32, u32, u32, u32, u32, vp, i64]
+    return lib
 
+
+def run_emu(lib, product, packed, off, lens, k, lo, hi, stride=1, table_lg=11):
+    """Candidates of the emulated product ("sort" or "rows"); None when the
+    row-wise tables overflow."""
+    packed = np.ascontiguousarray(packed, np.uint32)
+    off = np.ascontiguousarray(off, np.uint64)
+    lens = np.ascontiguousarray(lens, np.uint32)
+    args = [packed.ctypes.data, off.ctypes.data, lens.ctypes.data, len(lens), k, stride, lo, hi]
+    if product == "rows":
+        fn = lambda o, c: lib.emulate_candidates_rowwise(*args, table_lg, o, c)  # noqa: E731
+    else:
+        fn = lambda o, c: lib.emulate_candidates(*args, o, c)  # noqa: E731
+    n = fn(None, 0)
+    if n < 0:
+        return None
+    out = np.zeros(6 * max(n, 1), np.uint32)
+    assert fn(out.ctypes.data, n) == n
+    return out[:6 * n].view(S.CANDIDATE)
+
+
+@pytest.fixture(scope="module", params=["sort", "rows"])
+def emu(lib, request):
     def run(packed, off, lens, k, lo, hi, stride=1):
-        packed = np.ascontiguousarray(packed, np.uint32)
-        off = np.ascontiguousarray(off, np.uint64)
-        lens = np.ascontiguousarray(lens, np.uint32)
-        args = [packed.ctypes.data, off.ctypes.data, lens.ctypes.data, len(lens), k, stride, lo, hi]
-        n = lib.emulate_candidates(*args, None, 0)
-        out = np.zeros(6 * max(n, 1), np.uint32)
-        assert lib.emulate_candidates(*args, out.ctypes.data, n) == n
-        return out[:6 * n].view(S.CANDIDATE)
-
+        got = run_emu(lib, request.param, packed, off, lens, k, lo, hi, stride)
+        assert got is not None
+        return got
     return run
 
 
@@ -126,3 +146,55 @@ def test_sequencing_reads_medium(emu):
         want = S.candidate_pairs(packed, off, lens, k=k, lo=lo, hi=hi)
         assert len(want) > 100 and (want["b"] >> 31).sum() > 20
         same(emu(packed, off, lens, k, lo, hi), want)
+
+
+def star_reads(n_leaves, seed=12, k=8):
+    """Read 0 holds many distinct k-mers; every other read is a copy of one
+    of them, round robin: read 0 pairs with all n_leaves reads while no
+    k-mer is held by more than a few reads."""
+    rng = np.random.default_rng(seed)
+    while True:
+        hub = rng.integers(0, 4, 160).astype(np.uint8)
+        codes = S.occurrences([hub.tolist()], k)
+        if len({c for c, *_ in codes}) == len(codes):   # distinct canonical k-mers
+            break
+    n_k = len(hub) - k + 1
+    reads = [hub] + [hub[i % n_k:i % n_k + k].copy() for i in range(n_leaves)]
+    return reads
+
+
+def test_row_tables_overflow_and_fit(lib):
+    """A read with more partners than its table has slots makes the
+    row-wise product give up (the library then runs the sort-based one);
+    with room to spare both products equal the oracle."""
+    packed, off, lens = pack(star_reads(40))
+    want = S.candidate_pairs(packed, off, lens, k=8, lo=1, hi=1024)
+    assert (want["a"] == 0).sum() == 40
+    assert run_emu(lib, "rows", packed, off, lens, 8, 1, 1024, table_lg=5) is None   # 32 slots
+    for lg in (6, 11):
+        same(run_emu(lib, "rows", packed, off, lens, 8, 1, 1024, table_lg=lg), want)
+    same(run_emu(lib, "sort", packed, off, lens, 8, 1, 1024), want)
+
+
+def test_row_tables_full_size_overflow(lib):
+    """2,100 partners of one read overflow the library's 2,048-slot table;
+    2,000 fit."""
+    packed, off, lens = pack(star_reads(2100))
+    assert run_emu(lib, "rows", packed, off, lens, 8, 1, 1024) is None
+    want = S.candidate_pairs(packed, off, lens, k=8, lo=1, hi=1024)
+    assert (want["a"] == 0).sum() == 2100
+    same(run_emu(lib, "sort", packed, off, lens, 8, 1, 1024), want)
+    packed, off, lens = pack(star_reads(2000))    # 2,000 partners fit (98% full)
+    want = S.candidate_pairs(packed, off, lens, k=8, lo=1, hi=1024)
+    same(run_emu(lib, "rows", packed, off, lens, 8, 1, 1024), want)
+
+
+def test_rows_with_small_tables_and_heavy_probing(lib):
+    """Tables just large enough (many collisions, long probe chains) still
+    give the oracle's candidates."""
+    reads = small_genome_reads(33, seed=77, glen=300, lo=40, hi=120, err=False)
+    packed, off, lens = pack(reads)
+    want = S.candidate_pairs(packed, off, lens, k=13, lo=1, hi=1024)
+    max_partners = max(np.bincount(want["a"], minlength=len(reads)))
+    lg = int(np.ceil(np.log2(max_partners)))
+    same(run_emu(lib, "rows", packed, off, lens, 13, 1, 1024, table_lg=lg), want)

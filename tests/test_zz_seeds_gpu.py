@@ -1,7 +1,9 @@
 """Seed discovery on the GPU (xdrop_find_candidates: reliable k-mers and
 candidate read pairs) against the oracle (oracle/seeds.py), record for
-record, and its candidates aligned through xdrop_submit_pairs against the
-oracle's alignments.  At the paper's parameters (k = 31, frequency window
+record, for both products (sort-based and row-wise, including the
+row-wise product's fallback when a read's table overflows), and its
+candidates aligned through xdrop_submit_pairs against the oracle's
+alignments.  At the paper's parameters (k = 31, frequency window
 [20, 50], 29x coverage) the output is checked by properties that hold at
 any size and against the CPU emulation of the same pipeline.  Collected
 after the other GPU files, so that a run stopping at the first failure has
@@ -39,10 +41,24 @@ def as_candidates(pairs, shared):
     return out
 
 
-def gpu(X, packed, off, lens, k, lo, hi, stride=1):
+def gpu(X, packed, off, lens, k, lo, hi, stride=1, rowwise=False, expect_product=None):
+    """Candidates from the library; checks which product ran (the row-wise
+    one unless a read overflows its table, or nothing to pair)."""
     with X.Aligner() as al:
-        return as_candidates(*al.find_candidates(packed, off, lens, k=k, lo=lo, hi=hi,
-                                                 stride=stride))
+        got = as_candidates(*al.find_candidates(packed, off, lens, k=k, lo=lo, hi=hi,
+                                                stride=stride, rowwise=rowwise))
+        st = X.xdrop_get_seed_stats(al.ctx)
+    assert st["candidates"] == len(got)
+    if expect_product is None:
+        expect_product = X.XDROP_SEEDS_ROWWISE if rowwise else X.XDROP_SEEDS_SORT
+    if st["runs"] > 0:
+        assert st["product"] == expect_product
+    return got
+
+
+@pytest.fixture(params=[False, True], ids=["sort", "rowwise"])
+def rowwise(request):
+    return request.param
 
 
 def same(got, want):
@@ -68,15 +84,15 @@ def small_genome_reads(n_reads, seed, glen=400, lo=20, hi=160, rc_frac=0.4, err=
 
 @pytest.mark.parametrize("k", [1, 3, 7, 16, 17, 31, 32])
 @pytest.mark.parametrize("stride", [1, 3])
-def test_small_sweep(X, k, stride):
+def test_small_sweep(X, k, stride, rowwise):
     reads = small_genome_reads(9, seed=k * 10 + stride, err=k < 15)
     packed, off, lens = pack(reads)
     for lo, hi in ((1, 1024), (2, 5)):
         want = S.candidate_pairs(packed, off, lens, k=k, lo=lo, hi=hi, stride=stride)
-        same(gpu(X, packed, off, lens, k, lo, hi, stride), want)
+        same(gpu(X, packed, off, lens, k, lo, hi, stride, rowwise), want)
 
 
-def test_repeats_short_and_empty_reads(X):
+def test_repeats_short_and_empty_reads(X, rowwise):
     rng = np.random.default_rng(5)
     unit = rng.integers(0, 4, 7).astype(np.uint8)
     reads = [np.tile(unit, 12)[:80], np.zeros(0, np.uint8), np.tile(unit, 9)[3:60],
@@ -85,7 +101,7 @@ def test_repeats_short_and_empty_reads(X):
     packed, off, lens = pack(reads)
     for k, lo, hi in ((5, 1, 1024), (9, 2, 30), (9, 20, 40), (4, 3, 1024)):
         want = S.candidate_pairs(packed, off, lens, k=k, lo=lo, hi=hi)
-        same(gpu(X, packed, off, lens, k, lo, hi), want)
+        same(gpu(X, packed, off, lens, k, lo, hi, rowwise=rowwise), want)
 
 
 def test_medium_read_set(X):
@@ -96,6 +112,7 @@ def test_medium_read_set(X):
         want = S.candidate_pairs(packed, off, lens, k=k, lo=lo, hi=hi)
         assert len(want) > 1000
         same(gpu(X, packed, off, lens, k, lo, hi), want)
+        same(gpu(X, packed, off, lens, k, lo, hi, rowwise=True), want)
 
 
 def test_candidates_align_like_the_oracle(X, orc):
@@ -123,8 +140,11 @@ def test_result_cache_and_errors(X):
         same(as_candidates(*X.xdrop_find_candidates(al.ctx, 13, 1, 1024)), want13)
         same(as_candidates(*X.xdrop_find_candidates(al.ctx, 9, 2, 6)), want9)   # new params
         same(as_candidates(*X.xdrop_find_candidates(al.ctx, 13, 1, 1024)), want13)
+        assert X.xdrop_get_seed_stats(al.ctx)["product"] == X.XDROP_SEEDS_SORT
+        same(as_candidates(*X.xdrop_find_candidates(al.ctx, 13, 1, 1024, rowwise=True)), want13)
+        assert X.xdrop_get_seed_stats(al.ctx)["product"] == X.XDROP_SEEDS_ROWWISE
         # a short output buffer gets the first records and the total
-        prm = X.KmerParams(13, 1, 1, 1024)
+        prm = X.KmerParams(13, 1, 1, 1024, 0)
         buf = np.zeros(3, X.PAIR_DTYPE)
         n = ctypes.c_size_t()
         assert X.load().xdrop_find_candidates(al.ctx, ctypes.byref(prm), X._p(buf), None, 3,
@@ -142,6 +162,9 @@ def test_result_cache_and_errors(X):
             with pytest.raises(X.XdropError) as e:
                 X.xdrop_find_candidates(al.ctx, k, lo, hi, stride)
             assert e.value.code == X.XDROP_EINVAL
+        bad = X.KmerParams(13, 1, 1, 10, 2)   # unknown product flag
+        assert X.load().xdrop_find_candidates(al.ctx, ctypes.byref(bad), None, None, 0,
+                                              ctypes.byref(n)) == X.XDROP_EINVAL
     with X.Aligner() as al:  # no resident reads
         with pytest.raises(X.XdropError) as e:
             X.xdrop_find_candidates(al.ctx, 13, 1, 10)
@@ -171,12 +194,37 @@ def emu(tmp_path_factory):
     return run
 
 
+def star_reads(n_leaves, seed=12, k=8):
+    """Read 0 holds many distinct k-mers; every other read is a copy of one
+    of them, round robin: read 0 pairs with all n_leaves reads."""
+    rng = np.random.default_rng(seed)
+    while True:
+        hub = rng.integers(0, 4, 160).astype(np.uint8)
+        codes = S.occurrences([hub.tolist()], k)
+        if len({c for c, *_ in codes}) == len(codes):
+            break
+    n_k = len(hub) - k + 1
+    return [hub] + [hub[i % n_k:i % n_k + k].copy() for i in range(n_leaves)]
+
+
+def test_rowwise_table_overflow_falls_back(X):
+    """2,100 partners of one read overflow the 2,048-slot table: the call
+    runs the sort-based product and still gives the oracle's candidates;
+    2,000 partners fit."""
+    for n_leaves, product in ((2100, X.XDROP_SEEDS_SORT), (2000, X.XDROP_SEEDS_ROWWISE)):
+        packed, off, lens = pack(star_reads(n_leaves))
+        want = S.candidate_pairs(packed, off, lens, k=8, lo=1, hi=1024)
+        assert (want["a"] == 0).sum() == n_leaves
+        same(gpu(X, packed, off, lens, 8, 1, 1024, rowwise=True, expect_product=product), want)
+
+
 def test_paper_parameters_29x(X, emu):
     """k = 31, window [20, 50], 29x coverage of a 100 kb genome with
     accurate reads (1% errors; at 12% almost no 31-mer reaches a count of
     20): about 3 Mb in 290 reads.  Every candidate is a pair a < b in
     order, its seed is an exact k-mer match on the named strand (sampled),
-    and the whole output equals the CPU emulation of the pipeline."""
+    and the whole output equals the CPU emulation of the pipeline; both
+    products agree."""
     packed, off, lens = W.sequencing_reads(100_000, 29, 10_000, 6_000, 1_000, seed=29,
                                            error_rate=0.01)
     packed = np.ascontiguousarray(packed, np.uint32)
@@ -198,3 +246,4 @@ def test_paper_parameters_29x(X, emu):
         sa, sb = int(c["seed_a"]), int(c["seed_b"])
         assert np.array_equal(a[sa:sa + 31], b[sb:sb + 31])
     same(got, emu(packed, off, lens, 31, 20, 50))
+    same(gpu(X, packed, off, lens, 31, 20, 50, rowwise=True), got)
