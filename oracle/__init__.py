@@ -10,6 +10,7 @@ from .oracle import (  # noqa: F401
     NO_BEST,
     ORC_PAIR,
     ORC_RESULT,
+    accept,
     align_pairs,
     best_seeds,
     build,

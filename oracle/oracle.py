@@ -168,3 +168,41 @@ def best_seeds(pairs, results, match=1):
         best[start:end] = winner
         start = end
     return best
+
+
+def accept(pairs, results, read_len, match=1, mismatch=-1, error_e4=1500, delta_e4=1000):
+    """BELLA-style adaptive acceptance of each aligned pair (Section "Related
+    works", BELLA paragraph: an adaptive threshold decides which X-drop
+    alignments are kept; the paper gives no formula, so this is the reading
+    fixed here, with every quantity an exact integer or rational):
+
+      - total = left_score + seed_len * match + right_score;
+      - L = the overlap the seed implies: min(seed_a, seed_b)
+        + min(len_a - seed_a, len_b - seed_b) (positions and length of b on
+        the strand the pair names);
+      - with error rate e = error_e4 / 10^4 per read, a column of the
+        overlap pairs two correct bases with probability phi = (1 - e)^2 and
+        scores match then, mismatch otherwise: the expected score is
+        L * (phi * match + (1 - phi) * mismatch);
+      - accepted iff status is 0 and total >= (1 - delta) * expected, with
+        delta = delta_e4 / 10^4.
+
+    Returns uint8 flags.  Python integers throughout (no rounding)."""
+    pairs = np.asarray(pairs)
+    results = np.asarray(results)
+    out = np.zeros(len(pairs), np.uint8)
+    q = 10 ** 4
+    for p in range(len(pairs)):
+        if int(results["status"][p]) != 0:
+            continue
+        a, b = int(pairs["a"][p]), int(pairs["b"][p]) & 0x7FFFFFFF
+        sa, sb = int(pairs["seed_a"][p]), int(pairs["seed_b"][p])
+        la, lb = int(read_len[a]), int(read_len[b])
+        L = min(sa, sb) + min(la - sa, lb - sb)
+        total = (int(results["left_score"][p]) + int(pairs["seed_len"][p]) * int(match)
+                 + int(results["right_score"][p]))
+        phi_q2 = (q - int(error_e4)) ** 2                    # phi * 10^8
+        exp_q2 = phi_q2 * int(match) + (q * q - phi_q2) * int(mismatch)
+        # total >= (1 - delta) * L * expected, scaled by 10^12
+        out[p] = 1 if total * q ** 3 >= (q - int(delta_e4)) * L * exp_q2 else 0
+    return out
