@@ -319,6 +319,32 @@ typedef struct {
 
 int xdrop_get_seed_stats(xdrop_ctx *c, xdrop_seed_stats *st);
 
+/* Adaptive acceptance of aligned pairs (Section "Related works", BELLA
+ * paragraph: an adaptive threshold decides which X-drop alignments are
+ * kept; the paper gives no formula, so this is the library's reading).
+ * For pair p with result r, accept[p] = 1 iff r.status is XDROP_STATUS_OK,
+ * both read ids are below n_reads, and
+ *   r.left_score + seed_len * match + r.right_score
+ *     >= (1 - delta) * L * (phi * match + (1 - phi) * mismatch),
+ * where L = min(seed_a, seed_b) + min(len_a - seed_a, len_b - seed_b) is the
+ * overlap the seed implies (b's length and positions on the strand the
+ * pair names), phi = (1 - e)^2 is the chance that an overlap column pairs
+ * two correct bases at per-read error rate e, e = error_e4 / 10^4 and
+ * delta = delta_e4 / 10^4.  The comparison is exact (integers).
+ * pairs, results, read_len and accept are device arrays (n entries,
+ * n_reads lengths, n flags); the kernel runs asynchronously on the
+ * context's stream after the work queued there.  XDROP_EINVAL for NULL
+ * arrays or error_e4 / delta_e4 above 10,000. */
+typedef struct {
+    int32_t match, mismatch; /* the scoring the pairs were aligned with */
+    uint32_t error_e4;       /* per-read error rate, units of 1e-4      */
+    uint32_t delta_e4;       /* slack below the expected score, 1e-4    */
+} xdrop_accept_params;
+
+int xdrop_accept_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_result *results,
+                        size_t n, const uint32_t *read_len, uint32_t n_reads,
+                        const xdrop_accept_params *p, uint8_t *accept);
+
 /* Task ids (2*pair + 1 for a right extension, 2*pair for a left one)
  * that the first band tier handed to a wider tier during the most recently
  * synced ticket.  Copies up to cap ids to dst (host memory) and the total

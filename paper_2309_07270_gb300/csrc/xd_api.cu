@@ -1025,6 +1025,23 @@ int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *
     return XDROP_OK;
 }
 
+int xdrop_accept_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_result *results,
+                        size_t n, const uint32_t *read_len, uint32_t n_reads,
+                        const xdrop_accept_params *p, uint8_t *accept)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    if (!p) return fail(XDROP_EINVAL, "NULL parameters");
+    if (p->error_e4 > 10000 || p->delta_e4 > 10000)
+        return fail(XDROP_EINVAL, "error_e4 and delta_e4 must be at most 10000");
+    if (n == 0) return XDROP_OK;
+    if (!pairs || !results || !read_len || !accept) return fail(XDROP_EINVAL, "NULL array");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    CK(launch_accept((const Pair *)pairs, (const int32_t *)results, read_len, n_reads, n,
+                     p->match, p->mismatch, p->error_e4, p->delta_e4, accept, c->stream));
+    return XDROP_OK;
+}
+
 int xdrop_get_seed_stats(xdrop_ctx *c, xdrop_seed_stats *st)
 {
     if (!c || !st) return fail(XDROP_EINVAL, "NULL argument");

@@ -70,6 +70,10 @@ int find_candidates(cudaStream_t s, int sm_count, size_t budget, const uint32_t 
                     const uint32_t *h_len, uint32_t k, uint32_t stride, uint32_t lo, uint32_t hi,
                     uint32_t flags, std::vector<Pair> &out_pairs,
                     std::vector<uint32_t> &out_shared, SeedStats &stats, std::string &err);
+// Adaptive acceptance flag of every aligned pair (xd_accept.cu).
+cudaError_t launch_accept(const Pair *pairs, const int32_t *results, const uint32_t *read_len,
+                          uint32_t n_reads, uint64_t n, int32_t match, int32_t mismatch,
+                          uint32_t error_e4, uint32_t delta_e4, uint8_t *accept, cudaStream_t s);
 cudaError_t launch_max_len(const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s);
 

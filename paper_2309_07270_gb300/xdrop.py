@@ -44,7 +44,7 @@ EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
            "xdrop_align_static", "xdrop_static_last_error", "xdrop_load_reads",
            "xdrop_submit_pairs", "xdrop_get_serve_stats", "xdrop_best_seeds_device",
-           "xdrop_find_candidates", "xdrop_get_seed_stats"]
+           "xdrop_find_candidates", "xdrop_get_seed_stats", "xdrop_accept_device"]
 
 
 class XdropError(RuntimeError):
@@ -78,6 +78,11 @@ class ServeStats(ctypes.Structure):
 class KmerParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_uint32), ("stride", ctypes.c_uint32),
                 ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class AcceptParams(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("error_e4", ctypes.c_uint32), ("delta_e4", ctypes.c_uint32)]
 
 
 class SeedStats(ctypes.Structure):
@@ -124,8 +129,10 @@ def load():
     lib.xdrop_find_candidates.argtypes = [vp, ctypes.POINTER(KmerParams), vp, vp, sz,
                                           ctypes.POINTER(sz)]
     lib.xdrop_get_seed_stats.argtypes = [vp, ctypes.POINTER(SeedStats)]
+    lib.xdrop_accept_device.argtypes = [vp, vp, vp, sz, vp, u32, ctypes.POINTER(AcceptParams), vp]
     for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats",
-                 "xdrop_best_seeds_device", "xdrop_find_candidates", "xdrop_get_seed_stats"):
+                 "xdrop_best_seeds_device", "xdrop_find_candidates", "xdrop_get_seed_stats",
+                 "xdrop_accept_device"):
         getattr(lib, name).restype = ctypes.c_int
     lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
                                        u32, vp, vp]
@@ -290,6 +297,13 @@ def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1, rowwise=False):
     return pairs, shared
 
 
+def xdrop_accept_device(ctx, pairs_ptr, results_ptr, n, read_len_ptr, n_reads, match, mismatch,
+                        error_e4, delta_e4, accept_ptr):
+    prm = AcceptParams(int(match), int(mismatch), int(error_e4), int(delta_e4))
+    _check(load().xdrop_accept_device(ctx, pairs_ptr, results_ptr, int(n), read_len_ptr,
+                                      int(n_reads), ctypes.byref(prm), accept_ptr), ctx)
+
+
 def xdrop_get_seed_stats(ctx) -> dict:
     st = SeedStats()
     _check(load().xdrop_get_seed_stats(ctx, ctypes.byref(st)), ctx)
@@ -359,6 +373,17 @@ class Aligner:
         (xdrop_find_candidates); the reads stay resident for submit_pairs."""
         xdrop_load_reads(self.ctx, packed, read_off, read_len)
         return xdrop_find_candidates(self.ctx, k, lo, hi, stride, rowwise)
+
+    def accept_device(self, dev, sc: Scoring, error_e4=1500, delta_e4=1000):
+        """Adaptive acceptance flag of every pair of `dev` from the results
+        in dev.out (see xdrop_accept_device); returns a uint8 torch tensor."""
+        import torch
+        acc = torch.zeros(max(dev.n_pairs, 1), dtype=torch.uint8, device=dev.packed.device)
+        xdrop_accept_device(self.ctx, dev.pairs.data_ptr(), dev.out.data_ptr(), dev.n_pairs,
+                            dev.read_len.data_ptr(), dev.read_len.numel(), sc.match, sc.mismatch,
+                            error_e4, delta_e4, acc.data_ptr())
+        torch.cuda.synchronize(dev.packed.device)
+        return acc[: dev.n_pairs]
 
     def count_cells_device(self, dev, sc: Scoring):
         import torch
