@@ -68,6 +68,8 @@ def parse():
                     help="genome length of the seed-discovery read set")
     ap.add_argument("--seeds-rowwise", action="store_true",
                     help="seed discovery with the row-wise product")
+    ap.add_argument("--no-seeds", action="store_true",
+                    help="skip the seed-discovery object of the default line")
     return ap.parse_args()
 
 
@@ -440,6 +442,10 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, args.cpu_seconds)
 
+    seeds = None
+    if rank == 0 and ws == 1 and not args.no_seeds:
+        seeds = seed_discovery_runs()
+
     if rank == 0:
         cfg = workload_config(w)
         if args.pairs:
@@ -457,6 +463,7 @@ def run_ours(args):
                 "gpu_launches": launches, "clocks": clocks, "plain": plain,
                 "batched_over_plain": (value / plain["value"]) if plain else None,
                 "serving": serving_runs[0] if serving_runs else None,
+                "seed_discovery": seeds,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     batched.close()
@@ -493,6 +500,34 @@ def run_serve_sweep(args):
                       "producers": 25, "batch_pairs": [1000, 20000],
                       "config": workload_config(w), "runs": runs}), flush=True)
     return 0
+
+
+def seed_discovery_runs(genome=1_000_000, timeout_s=240):
+    """Seed discovery (the upstream row: reliable 31-mers and candidate
+    pairs) beside the headline: both products on 29x reads of a genome of
+    `genome` bases, each timed by `bench.py --seeds` in a process of its
+    own, so that nothing there can touch the alignment numbers above.  A
+    failed run is reported, not raised."""
+    out = {"workload": f"reads-29x-genome{genome}-err1pct, k=31, window [20, 50]",
+           "timing": "CUDA events around the library's pipeline, median of 3 steps"}
+    keep = ("value", "unit", "ms_per_step", "host_ms_per_step", "product", "candidates",
+            "reverse_strand", "occurrences", "reads")
+    for name, extra in (("sort", []), ("rowwise", ["--seeds-rowwise"])):
+        cmd = [sys.executable, os.path.abspath(__file__), "--seeds", "--seeds-genome", str(genome),
+               "--steps", "3", "--warmup", "1"] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+        except subprocess.TimeoutExpired:
+            out[name] = {"error": f"no result within {timeout_s} s"}
+            continue
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode == 0 and lines:
+            d = json.loads(lines[-1])
+            out[name] = {k: d.get(k) for k in keep}
+        else:
+            tail = (r.stderr.strip().splitlines() or ["(no output)"])[-1]
+            out[name] = {"error": f"exit {r.returncode}: {tail[:300]}"}
+    return out
 
 
 def run_seeds(args):
