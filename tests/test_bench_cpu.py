@@ -50,3 +50,35 @@ def test_committed_traffic_file_parses():
         assert f["kernel"].startswith("lockstep")
         assert len(f["source_sha"]) == 16
         assert float(f["dram_bytes_per_launch"]) > 0
+
+
+def test_committed_traffic_matches_the_current_kernel_sources():
+    """The DRAM traffic in profiles/traffic.txt was measured on the kernel
+    sources as they are: the default bench line can use it."""
+    bench = load_bench()
+    assert bench.traffic_from_profile("lockstep16_kernel<4,8>") is not None
+
+
+def test_seed_discovery_failure_is_reported_not_raised(monkeypatch):
+    """A seed-discovery run that fails (here: its child process exits 1)
+    becomes an error entry of the line's seed_discovery object."""
+    bench = load_bench()
+
+    class Done:
+        returncode = 1
+        stdout = "build ok\n"
+        stderr = "Traceback ...\nRuntimeError: no device\n"
+
+    monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: Done())
+    out = bench.seed_discovery_runs(genome=1000, timeout_s=5)
+    assert out["sort"] == {"error": "exit 1: RuntimeError: no device"}
+    assert out["rowwise"]["error"].startswith("exit 1")
+
+    class Good:
+        returncode = 0
+        stdout = '{"value": 5.0, "unit": "occurrences/s", "ms_per_step": 2.0, "product": "sort"}\n'
+        stderr = ""
+
+    monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: Good())
+    out = bench.seed_discovery_runs(genome=1000, timeout_s=5)
+    assert out["sort"]["value"] == 5.0 and out["rowwise"]["ms_per_step"] == 2.0
