@@ -280,7 +280,8 @@ int xdrop_best_seeds_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_r
  * and, unless shared is NULL, the number of shared reliable k-mers of each
  * to shared (host memory); *n = total.  The result stays in the context
  * until the read set or the parameters change, so a call with a larger cap
- * only copies.  Synchronous.  Limits: 1 <= k <= 32, stride >= 1,
+ * only copies.  Synchronous; other calls on the same context (serving
+ * submits too) wait until it returns.  Limits: 1 <= k <= 32, stride >= 1,
  * 1 <= lo <= hi <= 1024 (XDROP_EINVAL; also without resident reads);
  * fewer than 2^31 occurrences and 2^31 (pair, shared k-mer) entries, and
  * the context's memory budget (XDROP_ENOMEM).
