@@ -103,3 +103,19 @@ def test_seed_position_in_a_decides_alone():
         pos_a = [by_read[a][m] for m in shared]
         assert len(pos_a) == len(set(pos_a)) == c["shared"]
         assert min(pos_a) == c["seed_a"]
+
+
+def test_hand_case_golden():
+    """The worked example of tests/golden/seeds_hand_case.md, derived by hand."""
+    rc = S.PAIR_RC
+    reads = [W.encode("ACGTA"), W.encode("CGTAC"), W.encode("GGGG")]
+    packed, off, lens = pack(reads)
+    for stride, lo, hi, want in ((1, 2, 3, [(0, 1 | rc, 0, 2, 3, 2)]),
+                                 (1, 3, 3, [(0, 1 | rc, 0, 2, 3, 2)]),
+                                 (1, 2, 2, []),
+                                 (2, 2, 3, [(0, 1 | rc, 0, 2, 3, 2)])):
+        got = S.candidate_pairs(packed, off, lens, k=3, lo=lo, hi=hi, stride=stride)
+        assert got.tolist() == want, (stride, lo, hi)
+    reads[1] = W.encode("GTACG")
+    packed, off, lens = pack(reads)
+    assert S.candidate_pairs(packed, off, lens, k=3, lo=2, hi=3).tolist() == [(0, 1, 0, 2, 3, 2)]
