@@ -27,6 +27,7 @@
 
 #include "../../include/xdrop.h"
 #include "xd_launch.h"
+#include "xd_seeds.cuh"
 #include "xd_serve.h"
 
 using namespace xd;
@@ -994,7 +995,8 @@ int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *
 {
     if (!c) return fail(XDROP_EINVAL, "context is NULL");
     if (!p || !n || (cap && !pairs)) return fail(XDROP_EINVAL, "NULL argument");
-    if (p->k < 1 || p->k > 32 || p->stride < 1 || p->lo < 1 || p->lo > p->hi || p->hi > 1024 ||
+    if (p->k < 1 || p->k > xs::kMaxK || p->stride < 1 || p->lo < 1 || p->lo > p->hi ||
+        p->hi > xs::kMaxHi ||
         (p->flags & ~XDROP_SEEDS_ROWWISE))
         return fail(XDROP_EINVAL,
                     "k-mer parameters out of range (k %u, stride %u, lo %u, hi %u, flags %u)", p->k,

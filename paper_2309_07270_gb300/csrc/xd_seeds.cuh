@@ -28,7 +28,7 @@
 namespace xs {
 
 constexpr uint32_t kPairRC = 0x80000000u;
-constexpr uint32_t kMaxK = 32;
+constexpr uint32_t kMaxK = 32;     // codes fit 64 bits
 constexpr uint32_t kMaxHi = 1024;  // bounds the pairs one k-mer can make
 
 // One shared reliable k-mer of a read pair, and after the reduction by
@@ -227,7 +227,6 @@ XS_HD void run_members(const uint32_t *occ, const uint32_t *occ_rd, const uint32
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kTableLg = 11;  // 2,048 partners per read in shared memory
-constexpr uint32_t kOverflow = 0xFFFFFFFFu;
 
 struct RowTable {
     uint32_t *key;            // partner read id, kEmpty when free
