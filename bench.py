@@ -511,7 +511,7 @@ def seed_discovery_runs(genome=1_000_000, timeout_s=240):
     out = {"workload": f"reads-29x-genome{genome}-err1pct, k=31, window [20, 50]",
            "timing": "CUDA events around the library's pipeline, median of 3 steps"}
     keep = ("value", "unit", "ms_per_step", "host_ms_per_step", "product", "candidates",
-            "reverse_strand", "occurrences", "reads")
+            "reverse_strand", "candidates_sha256", "occurrences", "reads")
     for name, extra in (("sort", []), ("rowwise", ["--seeds-rowwise"])):
         cmd = [sys.executable, os.path.abspath(__file__), "--seeds", "--seeds-genome", str(genome),
                "--steps", "3", "--warmup", "1"] + extra
@@ -527,6 +527,8 @@ def seed_discovery_runs(genome=1_000_000, timeout_s=240):
         else:
             tail = (r.stderr.strip().splitlines() or ["(no output)"])[-1]
             out[name] = {"error": f"exit {r.returncode}: {tail[:300]}"}
+    digests = [out[n].get("candidates_sha256") for n in ("sort", "rowwise")]
+    out["products_agree"] = (digests[0] == digests[1]) if all(digests) else None
     return out
 
 
@@ -555,7 +557,7 @@ def run_seeds(args):
         for step in range(args.warmup + args.steps):
             X.xdrop_load_reads(al.ctx, packed, off, lens)
             t0 = time.perf_counter()
-            pairs, _ = X.xdrop_find_candidates(al.ctx, k, lo, hi, 1, args.seeds_rowwise)
+            pairs, shared = X.xdrop_find_candidates(al.ctx, k, lo, hi, 1, args.seeds_rowwise)
             dt = time.perf_counter() - t0
             st = X.xdrop_get_seed_stats(al.ctx)
             if step >= args.warmup:
@@ -570,6 +572,8 @@ def run_seeds(args):
                       "warmup": args.warmup, "higher_is_better": True,
                       "product": "+".join(sorted(names[p] for p in products)),
                       "candidates": int(len(pairs)), "reverse_strand": int((pairs["b"] >> 31).sum()),
+                      "candidates_sha256": hashlib.sha256(pairs.tobytes() + shared.tobytes())
+                      .hexdigest()[:16],
                       "reads": int(len(lens)), "occurrences": n_occ, "data": "synthetic",
                       "config": {"workload": f"reads-29x-genome{args.seeds_genome}-err1pct",
                                  "timing": "CUDA events around the library's pipeline"}}),

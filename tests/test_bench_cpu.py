@@ -74,11 +74,15 @@ def test_seed_discovery_failure_is_reported_not_raised(monkeypatch):
     assert out["sort"] == {"error": "exit 1: RuntimeError: no device"}
     assert out["rowwise"]["error"].startswith("exit 1")
 
+    assert out["products_agree"] is None
+
     class Good:
         returncode = 0
-        stdout = '{"value": 5.0, "unit": "occurrences/s", "ms_per_step": 2.0, "product": "sort"}\n'
+        stdout = ('{"value": 5.0, "unit": "occurrences/s", "ms_per_step": 2.0, "product": "sort", '
+                  '"candidates_sha256": "00ff"}\n')
         stderr = ""
 
     monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: Good())
     out = bench.seed_discovery_runs(genome=1000, timeout_s=5)
     assert out["sort"]["value"] == 5.0 and out["rowwise"]["ms_per_step"] == 2.0
+    assert out["products_agree"] is True
