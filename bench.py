@@ -70,6 +70,8 @@ def parse():
                     help="seed discovery with the row-wise product")
     ap.add_argument("--no-seeds", action="store_true",
                     help="skip the seed-discovery object of the default line")
+    ap.add_argument("--seeds-cpu", action="store_true",
+                    help="with --seeds: also time the oracle on a 20 kb-genome sample")
     return ap.parse_args()
 
 
@@ -511,8 +513,8 @@ def seed_discovery_runs(genome=1_000_000, timeout_s=240):
     out = {"workload": f"reads-29x-genome{genome}-err1pct, k=31, window [20, 50]",
            "timing": "CUDA events around the library's pipeline, median of 3 steps"}
     keep = ("value", "unit", "ms_per_step", "host_ms_per_step", "product", "candidates",
-            "reverse_strand", "candidates_sha256", "occurrences", "reads")
-    for name, extra in (("sort", []), ("rowwise", ["--seeds-rowwise"])):
+            "reverse_strand", "candidates_sha256", "occurrences", "reads", "cpu_baseline")
+    for name, extra in (("sort", ["--seeds-cpu"]), ("rowwise", ["--seeds-rowwise"])):
         cmd = [sys.executable, os.path.abspath(__file__), "--seeds", "--seeds-genome", str(genome),
                "--steps", "3", "--warmup", "1"] + extra
         try:
@@ -565,6 +567,18 @@ def run_seeds(args):
                 dev.append(st["ms"])
                 products.add(st["product"])
     ms = statistics.median(dev)
+    cpu = None
+    if args.seeds_cpu:  # the oracle as it stands, one core, on a small read set of the same recipe
+        from oracle import seeds as S
+        g = 20_000
+        sp, so, sl = W.sequencing_reads(g, 29, 10_000, 6_000, 1_000, seed=29, error_rate=0.01)
+        s_occ = int(np.maximum(sl.astype(np.int64) - (k - 1), 0).sum())
+        t0 = time.perf_counter()
+        S.candidate_pairs(sp, so, sl, k=k, lo=lo, hi=hi)
+        dt = time.perf_counter() - t0
+        cpu = {"value": s_occ / dt, "unit": "occurrences/s", "cores": 1, "kind": "oracle",
+               "sample": f"29x reads of a {g}-base genome, 1% errors ({s_occ} occurrences), "
+                         f"one call, {dt:.1f} s"}
     names = {X.XDROP_SEEDS_SORT: "sort", X.XDROP_SEEDS_ROWWISE: "rowwise"}
     print(json.dumps({"metric": f"seed discovery, k-mer occurrences/s (k={k}, window [{lo}, {hi}])",
                       "value": n_occ / (ms * 1e-3), "unit": "occurrences/s", "ms_per_step": ms,
@@ -574,6 +588,7 @@ def run_seeds(args):
                       "candidates": int(len(pairs)), "reverse_strand": int((pairs["b"] >> 31).sum()),
                       "candidates_sha256": hashlib.sha256(pairs.tobytes() + shared.tobytes())
                       .hexdigest()[:16],
+                      "cpu_baseline": cpu,
                       "reads": int(len(lens)), "occurrences": n_occ, "data": "synthetic",
                       "config": {"workload": f"reads-29x-genome{args.seeds_genome}-err1pct",
                                  "timing": "CUDA events around the library's pipeline"}}),
