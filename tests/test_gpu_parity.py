@@ -246,59 +246,6 @@ def test_modes_agree_and_repeat(X, aligners):
         assert np.array_equal(r[0], r[k])
 
 
-@pytest.fixture(scope="module")
-def genome29():
-    return W.genome_overlaps()
-
-
-@pytest.mark.parametrize("x", [50, 100])
-def test_genome_29x_full_size_sampled(X, aligners, orc, genome29, x):
-    """The full 29x overlap workload (about 314k pairs), batched device
-    submit as the benchmark runs it; 1200 sampled pairs against the oracle,
-    plus identical results from the host-memory submit on a slice."""
-    w = genome29.with_x(x)
-    dev = X.DeviceInputs.from_workload(w)
-    al = aligners["batched"]
-    al.align_device(dev, X.scoring(1, -1, -1, x))
-    got = dev.results()
-    assert (got["status"] == 0).all()
-    rng = np.random.default_rng(x)
-    idx = np.sort(rng.choice(w.n_pairs, 1200, replace=False))
-    want = oracle_results(orc, w.subset(idx), nthreads=16)
-    assert_same(got[idx], want, f"29x x={x}")
-    host = run_host(X, al, w.subset(np.arange(0, w.n_pairs, 97)))
-    assert np.array_equal(host, got[::97])
-
-
-@pytest.mark.parametrize("x", [50, 100])
-def test_genome_29x_every_pair_every_tile(X, orc, genome29, x):
-    """Every pair of the full 29x workload: each packed tile gives exactly
-    the results of the 32-bit 4x16 tile (whose sample the oracle checks in
-    the test above); any pair where the tiles disagree is also checked
-    against the oracle so that the failure names the wrong one."""
-    w = genome29.with_x(x)
-    dev = X.DeviceInputs.from_workload(w)
-    sc = X.scoring(1, -1, -1, x)
-    tiles = [(4, 16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16),
-             (4, 8 | P16), (2, 16 | P16)]
-    res = {}
-    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
-        for t in tiles:
-            al.set_tile(*t)
-            al.align_device(dev, sc)
-            assert al.tile() == t
-            res[t] = dev.results().view(np.int32).reshape(-1, 7).copy()
-    ref = res[tiles[0]]
-    bad = np.zeros(w.n_pairs, bool)
-    for t in tiles[1:]:
-        bad |= (res[t] != ref).any(axis=1)
-    idx = np.flatnonzero(bad)
-    if idx.size:
-        want = oracle_results(orc, w.subset(idx[:50]), nthreads=16).view(np.int32).reshape(-1, 7)
-        wrong = {tile_id(t): int((res[t][idx[:50]] != want).any(axis=1).sum()) for t in tiles}
-        pytest.fail(f"{idx.size} pairs differ between tiles; wrong of the first 50: {wrong}")
-
-
 @pytest.mark.parametrize("mode", MODES)
 def test_reverse_strand_pairs(X, aligners, orc, mode):
     """Half the pairs on the reverse strand (read b stored reverse-

@@ -1,7 +1,7 @@
 """Seed discovery on the GPU (xdrop_find_candidates: reliable k-mers and
 candidate read pairs) against the oracle (oracle/seeds.py), record for
 record (the default, sort-based product; the row-wise one is tested in
-test_zzzz_seeds_rowwise_gpu.py), and its candidates aligned through
+test_gpu_seeds_rowwise.py), and its candidates aligned through
 xdrop_submit_pairs against the oracle's alignments.  At the paper's parameters (k = 31, frequency window
 [20, 50], 29x coverage) the output is checked by properties that hold at
 any size and against the CPU emulation of the same pipeline.  Collected

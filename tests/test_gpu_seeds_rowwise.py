@@ -8,7 +8,7 @@ import pytest
 from oracle import seeds as S
 from paper_2309_07270_gb300 import workloads as W
 
-from test_zz_seeds_gpu import (X, as_candidates, gpu, pack, repeat_reads,  # noqa: F401
+from test_gpu_seeds import (X, as_candidates, gpu, pack, repeat_reads,  # noqa: F401
                                same, small_genome_reads)
 
 pytestmark = pytest.mark.gpu
