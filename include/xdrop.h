@@ -377,11 +377,12 @@ int xdrop_count_cells_device(xdrop_ctx *c, const uint32_t *packed,
  * returns without waiting: results are in `out` once that stream has
  * reached this point.  No context is needed and no device memory is
  * allocated: the scratch is a static 32 MiB array inside the library that
- * every device using the library holds until the process exits.  The first
- * call on a device looks the array up (make that first call before any
- * stream capture that should contain later calls).  All calls on a device
- * share the array: calls whose work may overlap on the GPU race and must
- * be ordered (same stream, or events).  Every extension runs on the
+ * every device using the library holds until the process exits.  Every
+ * call looks up the array's address on the current device; the first call
+ * on a device also loads the library's device code there, so make that
+ * first call before any stream capture that should contain later calls.
+ * All calls on a device share the array: calls whose work may overlap on
+ * the GPU race and must be ordered (same stream, or events).  Every extension runs on the
  * unbounded-band tier (one CTA per extension), which is exact for any band
  * but slower than the batched path.
  *
@@ -389,9 +390,10 @@ int xdrop_count_cells_device(xdrop_ctx *c, const uint32_t *packed,
  * (3*(max_read_len+1) int32 per extension) and values above 2,796,202
  * return XDROP_EINVAL.  Pairs that fail the limits get status
  * XDROP_STATUS_INVALID and zero scores; an extension longer than
- * max_read_len allows gets XDROP_STATUS_TOO_LONG.  Returns XDROP_OK once
- * the work is enqueued, XDROP_EINVAL for bad arguments, XDROP_ECUDA if the
- * launch failed (message from xdrop_static_last_error). */
+ * max_read_len allows gets XDROP_STATUS_TOO_LONG and zeros in that side's
+ * score and coordinates.  Returns XDROP_OK once the work is enqueued,
+ * XDROP_EINVAL for bad arguments, XDROP_ECUDA if the launch failed
+ * (message from xdrop_static_last_error). */
 int xdrop_align_static(const uint32_t *packed, uint64_t n_words,
                        const uint64_t *read_off, const uint32_t *read_len,
                        uint32_t n_reads, const xdrop_pair *pairs, size_t n_pairs,

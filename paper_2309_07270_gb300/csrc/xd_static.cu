@@ -20,7 +20,6 @@
 
 #include <algorithm>
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "xd_device.cuh"
@@ -36,7 +35,8 @@ static __device__ __align__(256) int32_t g_static_scratch[kStaticScratchWords];
 // One CTA per task (all 2*n_pairs tasks, grid-stride), each CTA with its
 // own slice of the static scratch.  Pairs that fail the limits get status
 // XDROP_STATUS_INVALID and zero scores; a task whose extension is longer
-// than the slice allows gets status XDROP_STATUS_TOO_LONG.
+// than the slice allows gets status XDROP_STATUS_TOO_LONG and zeros in its
+// side's three fields.
 __global__ void __launch_bounds__(WIDE_THREADS)
 static_wide_kernel(Job J, int32_t *scratch, int64_t per_cta)
 {
@@ -54,7 +54,10 @@ static_wide_kernel(Job J, int32_t *scratch, int64_t per_cta)
             continue;
         }
         if ((int64_t)3 * (e.m + 1) > per_cta) {
-            if (threadIdx.x == 0) atomicOr(&o[6], XDROP_STATUS_TOO_LONG);
+            if (threadIdx.x == 0) {
+                for (int k = 0; k < 3; ++k) o[3 * e.side + k] = 0;
+                atomicOr(&o[6], XDROP_STATUS_TOO_LONG);
+            }
             continue;
         }
         int32_t sc, bi, bj;
@@ -88,12 +91,6 @@ int static_fail(int code, const char *msg, cudaError_t e = cudaSuccess)
     return code;
 }
 
-// Device address of the static scratch, looked up once per device (with
-// that device current) on the first call made on it.
-constexpr int kMaxDevices = 64;
-std::mutex g_sym_mu;
-int32_t *g_sym_ptr[kMaxDevices] = {};
-
 }  // namespace
 
 extern "C" int xdrop_align_static(const uint32_t *packed, uint64_t n_words,
@@ -121,21 +118,16 @@ extern "C" int xdrop_align_static(const uint32_t *packed, uint64_t n_words,
                  max_read_len, (long long)(kStaticScratchWords / 3 - 1));
         return static_fail(XDROP_EINVAL, msg);
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return static_fail(XDROP_ECUDA, "cudaGetDevice", e);
-    if (dev < 0 || dev >= kMaxDevices) return static_fail(XDROP_EINVAL, "device index too large");
-    int32_t *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_sym_mu);
-        if (!g_sym_ptr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_static_scratch);
-            if (e != cudaSuccess) return static_fail(XDROP_ECUDA, "cudaGetSymbolAddress", e);
-            g_sym_ptr[dev] = (int32_t *)p;
-        }
-        scratch = g_sym_ptr[dev];
-    }
+    // In host code g_static_scratch names a host-side stand-in, not device
+    // memory: the kernel gets the array's address on the current device,
+    // looked up on every call (with that device current) so that a context
+    // re-created after a device reset never sees a stale address.  The
+    // first lookup on a device loads the module there, which is why the
+    // first call on a device must come before any stream capture.
+    void *sym = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&sym, g_static_scratch);
+    if (e != cudaSuccess) return static_fail(XDROP_ECUDA, "cudaGetSymbolAddress", e);
+    int32_t *scratch = (int32_t *)sym;
     int64_t per_cta = (per_task + 63) / 64 * 64;
     int grid = (int)std::min<int64_t>(kStaticMaxCtas, kStaticScratchWords / per_cta);
     if (grid < 1) grid = 1, per_cta = kStaticScratchWords;
