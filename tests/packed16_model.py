@@ -3,22 +3,24 @@
 This is neither the oracle nor the CUDA path: it restates, in plain Python
 integers, the arithmetic that ``lockstep16_loop`` in
 ``paper_2309_07270_gb300/csrc/xd_lockstep16.cuh`` performs for one group of
-lanes (two window slots per 32-bit register, s16x2 max / add-max, byte
-permutes, the normalised and scaled frame, rebasing, the packed key and the
-window shifts), so that ``test_packed16_model.py`` can check on the CPU that
-this arithmetic reaches the oracle's result exactly and never wraps a 16-bit
-half.  Any change to the kernel's arithmetic must be made here too.
+lanes (two window slots per 32-bit register, s16x2 max / add-max and plain
+32-bit adds of packed halves, byte permutes, the normalised and scaled
+frame, rebasing, the packed key, the window-edge test after every pair of
+diagonals and the window shifts), so that ``test_packed16_model.py`` can
+check on the CPU that this arithmetic reaches the oracle's result exactly,
+never wraps a 16-bit half and never carries from one half into the other.
+Any change to the kernel's arithmetic must be made here too.
 """
 
 M32 = 0xFFFFFFFF
 SCALE = 16            # stored value = 16 * r
-DEAD = -512 * SCALE   # stored value of a pruned slot
-DEAD2 = 0xE000E000
-REBASE = 256          # frame step, in units of r
+DEAD = -256 * SCALE   # stored value of a pruned slot
+DEAD2 = 0xF000F000
 
 
 class Wrap(AssertionError):
-    """A 16-bit half overflowed: the kernel would have computed garbage."""
+    """A 16-bit half overflowed, or a 32-bit add carried from the low half
+    into the high one: the kernel would have computed garbage."""
 
 
 def s16(v):
@@ -48,6 +50,7 @@ def prmt(a, b, sel):
 
 
 def add2(a, b):
+    """DPX-style per-half add (no carry between halves); wrap is an error."""
     la, ha = halves(a)
     lb, hb = halves(b)
     for v in (la + lb, ha + hb):
@@ -56,10 +59,22 @@ def add2(a, b):
     return mk(la + lb, ha + hb)
 
 
+def iadd32(a, b):
+    """A plain 32-bit add of two packed registers: exact per half only when
+    the low halves, read unsigned, do not carry and neither half wraps."""
+    if (a & 0xFFFF) + (b & 0xFFFF) > 0xFFFF:
+        raise Wrap("carry from the low half")
+    return add2(a, b)
+
+
 def max2(a, b):
     la, ha = halves(a)
     lb, hb = halves(b)
     return mk(max(la, lb), max(ha, hb))
+
+
+def max3(a, b, c):
+    return max2(max2(a, b), c)
 
 
 def addmax2(a, b, c):
@@ -72,7 +87,22 @@ def pack2(v):
 
 def fits(match, mismatch, gap, x):
     """The packed tiles' range (packed16_ok in the kernel)."""
-    return match - gap <= 128 and mismatch >= -128 and x >= 0 and x + match <= 1536
+    return (match - gap <= 128 and mismatch >= -128 and mismatch - 2 * gap >= 0 and x >= 0
+            and x + match <= 1536)
+
+
+def rebase_step(match, gap, x):
+    """The frame step of one rebase (rebase_step16 in the kernel)."""
+    ng = -gap
+    return min(1792, 1667 - 3 * ng - 2 * match, 2048 - x - 3 * match - 3 * ng)
+
+
+def live_lo(v):
+    return not v & 0x8000
+
+
+def live_hi(v):
+    return not v & 0x80000000
 
 
 def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
@@ -82,21 +112,24 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
     Returns (score, best_i, best_j, overflow); with overflow True the
     kernel would hand the task to a wider tier and the other fields are
     meaningless.  ``stats`` (a dict) receives counts of window shifts up
-    and down, rebases and masked diagonals."""
+    and down, rebases and masked pairs."""
     if stats is None:
         stats = {}
     for k in ("up", "down", "rebase", "masked"):
         stats.setdefault(k, 0)
+    assert fits(match, mismatch, gap, x)
     C2, S = regs, 2 * regs
     W = lanes * S
     m, n = len(a), len(b)
     ng = -gap
+    kR = rebase_step(match, gap, x)
+    assert kR >= 128
 
-    def base_a(i):  # 1-based; out-of-range positions get codes no base has
-        return int(a[i - 1]) if 1 <= i <= m else 4 + (i & 3)
+    def base_a(i):  # 1-based; out-of-range positions get arbitrary codes
+        return int(a[i - 1]) if 1 <= i <= m else (i * 7 + 1) & 3
 
     def base_b(j):
-        return int(b[j - 1]) if 1 <= j <= n else 8 + (j & 3)
+        return int(b[j - 1]) if 1 <= j <= n else (j * 5 + 2) & 3
 
     ma2 = pack2(SCALE * (match + 2 * ng))
     mi2 = pack2(SCALE * (mismatch + 2 * ng))
@@ -113,124 +146,140 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
     best = None  # (group key, window base i, diagonal)
     prev_dead = False
 
-    def margin():
+    def margin():  # diagonal pairs before a window cell can leave the rectangle
         return min(m - (i0[0] + W - 1), n - j0[0])
 
+    def diagonal(odd, masked):
+        """One anti-diagonal of the whole group; returns its group key."""
+        nonlocal d, Q, T, best
+        d += 1
+        Q += ng
+        for g in range(lanes):
+            if odd:
+                i0[g] += 1
+            else:
+                j0[g] += 1
+        if not masked and margin() < 0:
+            raise AssertionError("unmasked diagonal leaves the rectangle")
+        V, U = (O, E) if odd else (E, O)
+        thr = T + Q
+        nthr2 = pack2(-SCALE * thr)
+        lane_keys = []
+        newV = [list(v) for v in V]
+        for g in range(lanes):
+            xx = 0  # the kernel's base windows hold 2-bit fields
+            for s in range(16):
+                xx |= ((base_a(i0[g] + s) ^ base_b(j0[g] - s)) & 3) << (2 * s)
+            eq7 = ~(xx | (xx << 1)) & M32  # bit 2s+1: slot s matches
+            R = [(eq7 << (6 - 2 * q)) & M32 for q in range(4)]
+            if odd:
+                edge = U[g + 1][0] if g + 1 < lanes else DEAD2
+            else:
+                edge = U[g - 1][C2 - 1] if g > 0 else DEAD2
+            keys = []
+            for t in range(C2):
+                if odd:
+                    sh = U[g][t + 1] if t + 1 < C2 else prmt(U[g][0], edge, 0x5432)
+                else:
+                    sh = U[g][t - 1] if t > 0 else prmt(edge, U[g][C2 - 1], 0x5432)
+                sel = ((8 | (t >> 2)) | ((8 | (t >> 2)) << 4) |
+                       ((8 | ((t + C2) >> 2)) << 8) | ((8 | ((t + C2) >> 2)) << 12))
+                mk_ = prmt(R[t & 3], R[t & 3], sel)
+                s2 = (mk_ & ma2) | (~mk_ & mi2 & M32)
+                r = max3(iadd32(V[g][t], s2), U[g][t], sh)
+                if masked:
+                    # slot s lies in the rectangle iff lo <= s <= hi:
+                    # max(s - hi - 1, lo - 1 - s) < 0, bounds clamped to 16 bits
+                    lo, hi = j0[g] - n, m - i0[g]
+                    lo1_2 = pack2(min(max(lo - 1, -1024), 1024))
+                    nhi1_2 = pack2(min(max(-hi - 1, -1024), 1024))
+                    c = addmax2(mk(-t, -(t + C2)), lo1_2, 0x80008000)
+                    u = addmax2(mk(t, t + C2), nhi1_2, c)
+                    inside = prmt(u, u, 0xBB99)
+                    r = ((r & inside) | (DEAD2 & ~inside)) & M32
+                idx = (S - 1 - t) | ((S - 1 - (t + C2)) << 16)
+                kc = iadd32(idx, nthr2)
+                key = addmax2(r, kc, 0xFFF0FFF0)
+                pm = prmt(key, key, 0xBB99)
+                newV[g][t] = ((r & ~pm) | (DEAD2 & pm)) & M32
+                keys.append(key)
+            kk = keys[0]
+            for k_ in keys[1:]:
+                kk = max2(kk, k_)
+            lk = max(halves(kk))
+            lane_keys.append((lk >> 4) * 512 + ((lk & 15) | ((31 - g) << 4)))
+        for g in range(lanes):
+            V[g][:] = newV[g]
+        mkey = max(lane_keys)
+        if mkey >= (x + 1) * 512:  # the diagonal's best value exceeds T
+            T = T - x + (mkey >> 9)
+            best = (mkey, i0[0], d)
+        return mkey, thr
+
+    def shift(up):
+        if up:  # slot s takes slot s+1
+            ne = [E[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
+            no = [O[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
+            for g in range(lanes):
+                te, to = prmt(E[g][0], ne[g], 0x5432), prmt(O[g][0], no[g], 0x5432)
+                E[g], O[g] = E[g][1:] + [te], O[g][1:] + [to]
+                i0[g] += 1
+                j0[g] -= 1
+        else:   # slot s takes slot s-1
+            pe = [E[g - 1][C2 - 1] if g > 0 else DEAD2 for g in range(lanes)]
+            po = [O[g - 1][C2 - 1] if g > 0 else DEAD2 for g in range(lanes)]
+            for g in range(lanes):
+                te, to = prmt(pe[g], E[g][C2 - 1], 0x5432), prmt(po[g], O[g][C2 - 1], 0x5432)
+                E[g], O[g] = [te] + E[g][:-1], [to] + O[g][:-1]
+                i0[g] -= 1
+                j0[g] += 1
+
     budget = margin()
-    masked = budget < 2
     while True:
-        for odd in (True, False):
-            d += 1
-            Q += ng
-            budget -= 1
+        masked = budget < 1
+        stats["masked"] += masked
+        key_o, thr_o = diagonal(True, masked)
+        key_e, _ = diagonal(False, masked)
+        dead_o, dead_e = key_o < 0, key_e < 0
+        fin = (dead_o and (prev_dead or dead_e)) or d >= m + n
+        prev_dead = dead_e
+        budget -= 1
+        if fin:
+            if best is None:
+                return T, 0, 0, False
+            key, ibase, bd = best
+            bi = ibase + (31 - ((key >> 4) & 31)) * S + (S - 1 - (key & 15))
+            return T, bi, bd - bi, False
+        # Window edges after the even diagonal (live slots hold values >= 0,
+        # pruned ones DEAD < 0).  Up: the top slot of E (diagonal d) or of O
+        # (d-1) is live, and E's two bottom slots and O's bottom slot are
+        # dead.  Down: E's bottom slot is live and the two top slots of E
+        # and of O are dead.  Otherwise, with an edge live, the band has
+        # outgrown the window.
+        top, bot = lanes - 1, 0
+        need_up = live_hi(E[top][C2 - 1]) or live_hi(O[top][C2 - 1])
+        need_dn = live_lo(E[bot][0])
+        blk_up = live_lo(E[bot][0]) or live_lo(E[bot][1]) or live_lo(O[bot][0])
+        blk_dn = need_up or live_hi(E[top][C2 - 2]) or live_hi(O[top][C2 - 2])
+        if need_up:
+            if blk_up:
+                return T, 0, 0, True
+            stats["up"] += 1
+            shift(True)
+            budget = margin()
+        elif need_dn:
+            if blk_dn:
+                return T, 0, 0, True
+            stats["down"] += 1
+            shift(False)
+            budget = margin()
+        if thr_o >= kR:  # every live value is >= 16 kR: rebase the frame
+            stats["rebase"] += 1
+            mr = pack2(-SCALE * kR)
             for g in range(lanes):
-                if odd:
-                    i0[g] += 1
-                else:
-                    j0[g] += 1
-            if not masked and margin() < 0:
-                raise AssertionError("unmasked diagonal leaves the rectangle")
-            V, U = (O, E) if odd else (E, O)
-            stats["masked"] += masked
-            nthr2 = pack2(-SCALE * (T + Q))
-            lane_keys = []
-            for g in range(lanes):
-                eq = 0
-                for s in range(16):
-                    if base_a(i0[g] + s) == base_b(j0[g] - s):
-                        eq |= 1 << (2 * s)
-                R = [(eq << (7 - 2 * k)) & M32 for k in range(4)]
-                if odd:
-                    edge = U[g + 1][0] if g + 1 < lanes else DEAD2
-                else:
-                    edge = U[g - 1][C2 - 1] if g > 0 else DEAD2
-                keys, newV = [], list(V[g])
                 for t in range(C2):
-                    if odd:
-                        sh = U[g][t + 1] if t + 1 < C2 else prmt(U[g][0], edge, 0x5432)
-                    else:
-                        sh = U[g][t - 1] if t > 0 else prmt(edge, U[g][C2 - 1], 0x5432)
-                    nb = max2(U[g][t], sh)
-                    sel = ((8 | (t >> 2)) | ((8 | (t >> 2)) << 4) |
-                           ((8 | ((t + C2) >> 2)) << 8) | ((8 | ((t + C2) >> 2)) << 12))
-                    mk_ = prmt(R[t & 3], R[t & 3], sel)
-                    s2 = (mk_ & ma2) | (~mk_ & mi2 & M32)
-                    r = addmax2(V[g][t], s2, nb)
-                    if masked:
-                        # slot s lies in the rectangle iff lo <= s <= hi:
-                        # max(s - hi - 1, lo - 1 - s) < 0, bounds clamped to 16 bits
-                        lo, hi = j0[g] - n, m - i0[g]
-                        lo1_2 = pack2(min(max(lo - 1, -1024), 1024))
-                        nhi1_2 = pack2(min(max(-hi - 1, -1024), 1024))
-                        slot2 = mk(t, t + C2)
-                        nslot2 = mk(-t, -(t + C2))
-                        c = addmax2(nslot2, lo1_2, 0x80008000)
-                        u = addmax2(slot2, nhi1_2, c)
-                        inside = prmt(u, u, 0xBB99)
-                        r = ((r & inside) | (DEAD2 & ~inside)) & M32
-                    idx = (S - 1 - t) | ((S - 1 - (t + C2)) << 16)
-                    kc = addmax2(idx, nthr2, 0x80008000)
-                    key = addmax2(r, kc, 0xFFF0FFF0)
-                    pm = prmt(key, key, 0xBB99)
-                    newV[t] = ((r & ~pm) | (DEAD2 & pm)) & M32
-                    keys.append(key)
-                V[g][:] = newV
-                kk = keys[0]
-                for k_ in keys[1:]:
-                    kk = max2(kk, k_)
-                lk = max(halves(kk))
-                lane_keys.append((lk >> 4) * 512 + ((lk & 15) | ((31 - g) << 4)))
-            mkey = max(lane_keys)
-            xm = mkey >> 9
-            if xm > x:
-                T = T - x + xm
-                best = (mkey, i0[0], d)
-            dead = mkey < 0
-            fin = (dead and prev_dead) or d >= m + n
-            prev_dead = dead
-            dead16 = DEAD & 0xFFFF
-            # window edges: after an odd diagonal a live top slot may seed a
-            # cell above the window (shift up), after an even one a live
-            # bottom slot one below it (shift down); with the opposite edge
-            # live too the band outgrew the window
-            vtop, vbot = V[lanes - 1][C2 - 1] >> 16, V[0][0] & 0xFFFF
-            if not fin and (vtop if odd else vbot) != dead16:
-                if (vbot if odd else vtop) != dead16:
-                    return T, 0, 0, True
-                stats["up" if odd else "down"] += 1
-                if odd:  # shift up: slot s takes slot s+1
-                    ne = [E[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
-                    no = [O[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
-                    for g in range(lanes):
-                        te, to = prmt(E[g][0], ne[g], 0x5432), prmt(O[g][0], no[g], 0x5432)
-                        E[g], O[g] = E[g][1:] + [te], O[g][1:] + [to]
-                        i0[g] += 1
-                        j0[g] -= 1
-                else:    # shift down: slot s takes slot s-1
-                    pe = [E[g - 1][C2 - 1] if g > 0 else DEAD2 for g in range(lanes)]
-                    po = [O[g - 1][C2 - 1] if g > 0 else DEAD2 for g in range(lanes)]
-                    for g in range(lanes):
-                        te, to = prmt(pe[g], E[g][C2 - 1], 0x5432), prmt(po[g], O[g][C2 - 1], 0x5432)
-                        E[g], O[g] = [te] + E[g][:-1], [to] + O[g][:-1]
-                        i0[g] -= 1
-                        j0[g] += 1
-                if not masked:
-                    budget = margin()
-            if fin:
-                if best is None:
-                    return T, 0, 0, False
-                key, ibase, bd = best
-                bi = ibase + (31 - ((key >> 4) & 31)) * S + (S - 1 - (key & 15))
-                return T, bi, bd - bi, False
-            if not odd:
-                if T + Q + ng >= REBASE:
-                    stats["rebase"] += 1
-                    mr = pack2(-SCALE * REBASE)
-                    for g in range(lanes):
-                        for t in range(C2):
-                            E[g][t] = addmax2(E[g][t], mr, DEAD2)
-                            O[g][t] = addmax2(O[g][t], mr, DEAD2)
-                    Q -= REBASE
-                if not masked and budget < 2:
-                    budget = margin()
-                    masked = budget < 2
+                    E[g][t] = addmax2(E[g][t], mr, DEAD2)
+                    O[g][t] = addmax2(O[g][t], mr, DEAD2)
+            Q -= kR
+        if budget < 1:
+            budget = margin()

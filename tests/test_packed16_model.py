@@ -1,8 +1,9 @@
 """CPU check of the packed 16-bit band arithmetic against the oracle.
 
 ``packed16_model`` restates the kernel's 16-bit arithmetic bit by bit
-(two slots per register, s16x2 ops, normalised and scaled frame, rebases,
-packed keys, window shifts).  On seeded random extensions, including
+(two slots per register, s16x2 ops and carry-free 32-bit adds of packed
+halves, normalised and scaled frame, rebases, packed keys, window shifts
+decided once per pair of diagonals).  On seeded random extensions, including
 scorings at the edges of the packed range, it must reach the oracle's
 (score, best_i, best_j) exactly whenever the band fits the window, and no
 16-bit half may ever wrap.  This pins the exactness argument of the packed
@@ -21,7 +22,7 @@ SCORINGS = [
     (64, -128, -64, 1472),  # every limit at once
     (3, -2, -125, 100),     # the frame grows fastest through the gap
     (127, -1, -1, 1409),    # largest match
-    (1, -128, -1, 1535),    # largest x
+    (1, -2, -1, 1535),      # largest x, mismatch = 2 gap
     (7, -1, -2, 0),         # x = 0
 ]
 
@@ -46,6 +47,11 @@ def test_scorings_are_in_the_packed_range():
     assert all(P.fits(*sc) for sc in SCORINGS)
     assert not P.fits(1, -1, -1, 1536) and not P.fits(128, -1, -1, 10)
     assert not P.fits(1, -129, -1, 10) and not P.fits(1, -1, -128, 10)
+    assert not P.fits(1, -3, -1, 10)  # mismatch + 2|gap| < 0: 32-bit tiles
+    # the rebase step never falls below 128 inside the range
+    for match in range(1, 128):
+        for ng in range(1, 129 - match):
+            assert P.rebase_step(match, -ng, 1536 - match) >= 128
 
 
 @pytest.mark.parametrize("lanes,regs,seed", [(4, 8, 1), (8, 4, 2)])
@@ -93,7 +99,7 @@ def test_model_drifting_band_shifts_the_window(orc, lanes, regs):
     d = _drifting(t, rng, 8)
     shifted = {"up": 0, "down": 0}
     for a, b in [(t, d), (d, t)]:
-        for sc in [(1, -1, -1, 20), (2, -3, -1, 30)]:
+        for sc in [(1, -1, -1, 20), (2, -2, -1, 30)]:
             st = {}
             got = P.extend(a, b, *sc, lanes=lanes, regs=regs, stats=st)
             assert not got[3], (sc, lanes, regs)
