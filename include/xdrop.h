@@ -60,7 +60,9 @@ extern "C" {
 
 /* xdrop_init flags. */
 #define XDROP_MODE_BATCHED 0u /* default: binned persistent launch in a graph */
-#define XDROP_MODE_PLAIN 1u   /* one launch per 10,000-pair sub-batch         */
+#define XDROP_MODE_PLAIN 1u   /* one launch of the first band tile per
+                                 10,000-pair sub-batch, in pair order (the
+                                 forced tile, else packed 4x16)             */
 #define XDROP_MODE_SERVE 2u   /* batched, plus continuous batching of
                                  xdrop_submit_pairs requests (serving)       */
 
@@ -134,6 +136,9 @@ typedef struct {
     uint64_t spill_reserved;  /* extensions handed to the second tier        */
     uint64_t spill_taken;     /* of those, taken by second-tier groups       */
     uint64_t ring_warps;      /* first-tier warps of the running kernel      */
+    uint64_t idle_exits;      /* first-tier warps that left because no work
+                                 came within the idle bound (hang guard),
+                                 over all launches of the serving kernel    */
 } xdrop_serve_stats;
 
 /* Create a context on CUDA device `device`.  device_mem_budget bounds the
@@ -204,6 +209,15 @@ int xdrop_submit_pairs(xdrop_ctx *c, const xdrop_pair *pairs, size_t n_pairs,
 /* Counters of the serving loop (all zero outside serving mode). */
 int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st);
 
+/* Serving mode: the hang guard.  A group of the serving kernel that finds
+ * no work waits at most idle_ns nanoseconds (default 5 s; 0 restores it),
+ * then its warp leaves and counts itself in idle_exits; the kernel ends
+ * when every warp has left, and the next request launches it again.  The
+ * host normally stops an idle kernel after about 50 ms, so the bound only
+ * matters if that stop never arrives.  Takes effect at the next launch of
+ * the serving kernel.  Returns XDROP_OK, or XDROP_EINVAL for a NULL c. */
+int xdrop_set_serve_idle(xdrop_ctx *c, uint64_t idle_ns);
+
 /* Wait for a ticket.  timeout_ns < 0 waits without bound; otherwise the
  * call returns XDROP_ETIMEDOUT after about timeout_ns and the ticket stays
  * valid for a later sync.  Returns XDROP_OK once the results are in `out`,
@@ -223,18 +237,22 @@ void *xdrop_stream(xdrop_ctx *c);
 int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
 
 /* Packed tiles: 16-bit cells, two per 32-bit register, for scorings with
- * match - gap <= 128, mismatch >= -128 and x + match <= 1536 (results
- * identical to the 32-bit tiles; other scorings run the 32-bit tile of
- * the same shape).  Set in `cells` of xdrop_set_tile. */
+ * match - gap <= 128, mismatch >= -128, mismatch - 2*gap >= 0 and
+ * x + match <= 1536 (results identical to the 32-bit tiles; other
+ * scorings run the 32-bit tile of the same shape).  Set in `cells` of
+ * xdrop_set_tile. */
 #define XDROP_TILE_PACKED16 0x100
 
-/* Batched mode: fix the first band tier to `lanes` lanes per extension
+/* Batched and plain modes: fix the first band tier to `lanes` lanes per extension
  * and `cells` cells per lane (lanes*cells slots per anti-diagonal parity),
  * or pass lanes = 0 to go back to autotuning.  Autotuning (the default)
- * times the first-tier tiles on a sample of the first submit with a new
- * scoring (the packed tiles on a third of it when the scoring fits them,
- * else the 32-bit tiles on an eighth) and keeps the fastest for that
- * scoring.  Tiles: 4x16, 8x8, 16x4,
+ * keys the first tile by the scoring and the job's length bucket (the
+ * length bin, ceil(log2(max(m, n) + 1)) of an extension, that holds the
+ * median of the job's work, read from a device histogram at every batched
+ * submit).  The first submit with a new key times the first-tier tiles on
+ * a stratified random sample of its pairs (one pair of every 3 with the
+ * packed tiles when the scoring fits them, else one of every 8 with the
+ * 32-bit tiles) and keeps the fastest for that key.  Tiles: 4x16, 8x8, 16x4,
  * 8x16, 16x8, 32x4, and packed (cells | XDROP_TILE_PACKED16) 4x8, 2x16,
  * 4x16, 8x8, 8x16, 16x8.  Returns XDROP_EINVAL for another shape.  Serving mode
  * (set the tile before the first xdrop_submit_pairs) runs packed 4x16 by
@@ -286,21 +304,21 @@ int xdrop_best_seeds_device(xdrop_ctx *c, const xdrop_pair *pairs, const xdrop_r
  * fewer than 2^31 occurrences and 2^31 (pair, shared k-mer) entries, and
  * the context's memory budget (XDROP_ENOMEM).
  *
- * Two products compute the same candidates.  XDROP_SEEDS_SORT (default)
- * writes one entry per (read pair, shared reliable k-mer), sorts the
- * entries by pair and reduces them.  XDROP_SEEDS_ROWWISE builds A's rows
- * and columns and accumulates each read's partners in a shared-memory hash
- * table of 2,048 slots, one thread block per read, without per-entry
- * tables; a read with more partners than that makes the call run the
- * sort-based product instead.  xdrop_get_seed_stats tells which ran. */
-#define XDROP_SEEDS_SORT 0u
-#define XDROP_SEEDS_ROWWISE 1u
+ * Two products compute the same candidates.  XDROP_SEEDS_ROWWISE (default)
+ * builds A's rows and columns and accumulates each read's partners in a
+ * shared-memory hash table of 2,048 slots, one thread block per read,
+ * without per-entry tables; a read with more partners than that makes the
+ * call run the sort-based product instead.  XDROP_SEEDS_SORT writes one
+ * entry per (read pair, shared reliable k-mer), sorts the entries by pair
+ * and reduces them.  xdrop_get_seed_stats tells which ran. */
+#define XDROP_SEEDS_ROWWISE 0u
+#define XDROP_SEEDS_SORT 1u
 
 typedef struct {
     uint32_t k;      /* k-mer length                               */
     uint32_t stride; /* a k-mer starts at every stride-th position */
     uint32_t lo, hi; /* reliable iff lo <= count <= hi             */
-    uint32_t flags;  /* XDROP_SEEDS_SORT or XDROP_SEEDS_ROWWISE    */
+    uint32_t flags;  /* XDROP_SEEDS_ROWWISE or XDROP_SEEDS_SORT    */
 } xdrop_kmer_params;
 
 int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *pairs,
@@ -313,9 +331,11 @@ typedef struct {
     uint64_t occurrences; /* k-mer occurrences                             */
     uint64_t runs;        /* k-mers that occur at least twice              */
     uint64_t candidates;  /* candidate pairs                               */
-    uint32_t product;     /* XDROP_SEEDS_SORT or XDROP_SEEDS_ROWWISE: the
+    uint32_t product;     /* XDROP_SEEDS_ROWWISE or XDROP_SEEDS_SORT: the
                              product that produced them                    */
     uint32_t pad;
+    uint64_t nonzeros;    /* nonzeros of A (read, reliable k-mer), counted
+                             by the row-wise product; 0 if it did not run  */
 } xdrop_seed_stats;
 
 int xdrop_get_seed_stats(xdrop_ctx *c, xdrop_seed_stats *st);

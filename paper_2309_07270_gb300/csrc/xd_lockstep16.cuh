@@ -3,18 +3,20 @@
 // Same extension, same reading of the X-drop recurrence and the same
 // results as lockstep_loop (xd_device.cuh); only the arithmetic changes.
 // It is exact whenever the scoring passes packed16_ok():
-//   match - gap <= 128, mismatch >= -128, x + match <= 1536.
+//   match - gap <= 128, mismatch >= -128, mismatch + 2|gap| >= 0,
+//   x + match <= 1536.
 //
 // Normalised scores.  A cell on anti-diagonal d holds
-//   r = H + x + d*|gap| - B          (B: multiples of kRebase taken off)
+//   r = H + x + d*|gap| - B          (B: the rebase steps taken off)
 // stored as 16*r.  Then the two gap predecessors enter unchanged and the
-// diagonal one with s + 2|gap|:
+// diagonal one with s + 2|gap| >= 0:
 //   r(d) = max(r_diag(d-2) + s + 2|gap|,  r_up(d-1),  r_left(d-1)),
-// one DPX max and one DPX add-max per register (two cells).  The
-// threshold of diagonal d (T of d-1 minus x) becomes thr = T + d*|gap| - B,
-// a cell is live iff r >= thr, and r - thr <= x + match.
+// one plain 32-bit add (both halves at once, see below) and one DPX
+// three-way max per register (two cells).  The threshold of diagonal d
+// (T of d-1 minus x) becomes thr = T + d*|gap| - B, a cell is live iff
+// r >= thr, and r - thr <= x + match.
 //
-// Key.  One more DPX add-max gives each slot's key
+// Key.  One more 32-bit add and a DPX add-max give each slot's key
 //   16*(r - thr) + (S-1-slot), floored at -16,
 // which is negative exactly for the cells the X-drop test prunes (their
 // stored value becomes kDead by the key's sign mask) and, for live cells,
@@ -29,14 +31,34 @@
 // register t sits in register t+1 (t-1) at the same half; only the end
 // registers need a byte permute and one shuffle per diagonal.
 //
-// Ranges, in units of r (no 16-bit wrap anywhere, all values times 16 below
-// 2^15): the frame is rebased by kRebase = 256 once thr would reach it, and
-// thr grows by at most 2*(match+|gap|) <= 256 per diagonal pair, so thr
-// stays in [0, 512); live values stay at or below 511 + x + match <= 2047
-// and at or above -256 right after a rebase; dead slots hold -512, and a
-// value built from dead predecessors stays at or below -512 + match +
-// 2|gap| <= -256 < thr; the lowest value formed is above -640 and the
-// lowest key sum above -18432.
+// Ranges, in units of r, with kR the rebase step of the scoring
+// (rebase_step16, between 128 and 1792 inside the range above).  After
+// every pair of diagonals (odd d-1, even d) the frame is rebased by kR
+// once thr of d-1 reaches kR.  Every live value of d-1 and d is at least
+// that threshold, so live values stay >= 0 (>= thr >= 0) at all times and
+// pruned ones hold kDead = -256.  thr grows by at most 3|gap| + 2 match
+// over the three diagonals between two tests, so thr < kR + 3|gap| +
+// 2 match <= 1666 and every live value is at most thr + x + match <= 2047
+// (16 times that fits a signed half).  A value built from a pruned
+// predecessor stays below -256 + 255 < 0 <= thr.  No value formed is
+// below kDead (substitutions are >= 0 here), the lowest key sum is
+// 16 kDead/16 - 16 * 1666 > -32768, and a rebase takes kDead to
+// kDead - 16 kR >= -32768 before the floor restores it.
+//
+// Carry-free adds.  V + s2 (stored value plus packed substitution, s2 in
+// [0, 16*255]) and idx + (-16 thr) (idx <= 15 < 16 thr unless thr = 0) are
+// plain 32-bit adds: the low halves, read unsigned, never reach 2^16 (a
+// live half is < 2^15 - s2, kDead is 0xF000 and 0xF000 + 0x0FF0 < 2^16),
+// so nothing carries into the high half.
+//
+// Window edges.  Live values are >= 0 and pruned ones negative, so the
+// sign bit of a half tells whether that slot is live.  The edges are
+// tested once per pair of diagonals, after the even one: no live cell of
+// diagonals d+1, d+2 can leave the window unless E's top slot (diagonal d)
+// or O's top slot (d-1) is live, or E's bottom slot is.  The window then
+// shifts up one slot if E's two bottom slots and O's bottom slot are dead,
+// or down one slot if the two top slots of E and of O are dead; otherwise
+// the band has outgrown the window and the task goes to a wider tier.
 #pragma once
 #include <stdint.h>
 
@@ -49,9 +71,8 @@ namespace xd {
 namespace p16 {
 
 constexpr int32_t kScale = 16;            // stored value = 16 * r
-constexpr int32_t kDead = -512 * kScale;  // stored value of a pruned slot
-constexpr uint32_t kDead2 = 0xE000E000u;  // kDead in both halves
-constexpr int32_t kRebase = 256;          // frame step, in units of r
+constexpr int32_t kDead = -256 * kScale;  // stored value of a pruned slot
+constexpr uint32_t kDead2 = 0xF000F000u;  // kDead in both halves
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 {
@@ -60,7 +81,7 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
     return r;
 }
 
-__device__ __forceinline__ uint32_t pack2(int32_t v) { return ((uint32_t)v & 0xFFFFu) * 0x10001u; }
+__host__ __device__ inline uint32_t pack2(int32_t v) { return ((uint32_t)v & 0xFFFFu) * 0x10001u; }
 
 // Byte-permute selector giving 0xFFFF in the low half where slot t's match
 // bit is set and likewise in the high half for slot t+C2.  Match bits sit
@@ -111,26 +132,31 @@ __device__ __forceinline__ uint32_t tree_max2(const uint32_t (&k)[N])
     }
 }
 
+// A slot is live iff its half is non-negative (pruned slots hold kDead).
+__device__ __forceinline__ bool live_lo(uint32_t v) { return (v & 0x8000u) == 0; }
+__device__ __forceinline__ bool live_hi(uint32_t v) { return (int32_t)v >= 0; }
+
 // One anti-diagonal for one lane: V (diagonal d-2, overwritten with d) and
 // U (d-1).  edge: the neighbouring lane's end register of U (next lane's
 // register 0 on odd diagonals, previous lane's register C2-1 on even ones).
-// Returns the lane's 16-bit key, sign-extended.
+// eq7: bit 2s+1 set iff slot s's bases match.  Returns the lane's 16-bit
+// key, sign-extended.
 template <int C2, bool ODD, bool MASKED>
 __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
-                                        uint32_t edge, uint32_t eq, uint32_t ma2, uint32_t mi2,
+                                        uint32_t edge, uint32_t eq7, uint32_t ma2, uint32_t mi2,
                                         uint32_t nthr2, uint32_t lo1_2, uint32_t nhi1_2)
 {
-    const uint32_t R[4] = {eq << 7, eq << 5, eq << 3, eq << 1};
+    // R[q]: the match bit of slot 4b + q at the msb of byte b
+    const uint32_t R[4] = {eq7 << 6, eq7 << 4, eq7 << 2, eq7};
     uint32_t key[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) {
         uint32_t sh;
         if (ODD) sh = (t + 1 < C2) ? U[t + 1] : prmt(U[0], edge, 0x5432);
         else sh = (t > 0) ? U[t - 1] : prmt(edge, U[C2 - 1], 0x5432);
-        const uint32_t nb = __vmaxs2(U[t], sh);
         const uint32_t mk = prmt(R[t & 3], R[t & 3], mask_sel<C2>(t));
         const uint32_t s2 = (mk & ma2) | (~mk & mi2);
-        uint32_t r = __viaddmax_s16x2(V[t], s2, nb);
+        uint32_t r = __vimax3_s16x2(V[t] + s2, U[t], sh);  // carry-free add (header)
         if (MASKED) {
             // slot s lies in the rectangle iff lo <= s <= hi (lo = j0 - n,
             // hi = m - i0): max(s - hi - 1, lo - 1 - s) < 0, per half
@@ -140,8 +166,7 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
             r = (r & in) | (kDead2 & ~in);
         }
         // 16*(r - thr) + (S-1-slot), floored at -16: negative iff pruned
-        const uint32_t kc = __viaddmax_s16x2(idx2<C2>(t), nthr2, 0x80008000u);
-        const uint32_t k = __viaddmax_s16x2(r, kc, 0xFFF0FFF0u);
+        const uint32_t k = __viaddmax_s16x2(r, idx2<C2>(t) + nthr2, 0xFFF0FFF0u);
         const uint32_t pm = prmt(k, k, 0xBB99);  // 0xFFFF where pruned
         V[t] = (r & ~pm) | (kDead2 & pm);
         key[t] = k;
@@ -156,8 +181,19 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
 
 __host__ __device__ inline bool packed16_ok(const Scoring &sc)
 {
-    return sc.match - sc.gap <= 128 && sc.mismatch >= -128 && sc.x >= 0 &&
-           sc.x + sc.match <= 1536;
+    return sc.match - sc.gap <= 128 && sc.mismatch >= -128 && sc.mismatch - 2 * sc.gap >= 0 &&
+           sc.x >= 0 && sc.x + sc.match <= 1536;
+}
+
+// Frame step of one rebase (units of r) for a scoring that passes
+// packed16_ok: at least 128 there (see the header comment's ranges).
+__host__ __device__ inline int32_t rebase_step16(const Scoring &sc)
+{
+    const int32_t ng = -sc.gap;
+    int32_t k = 1792;
+    k = k < 1667 - 3 * ng - 2 * sc.match ? k : 1667 - 3 * ng - 2 * sc.match;
+    k = k < 2048 - sc.x - 3 * sc.match - 3 * ng ? k : 2048 - sc.x - 3 * sc.match - 3 * ng;
+    return k;
 }
 
 template <int L, int C2, class Src>
@@ -166,11 +202,12 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     using namespace p16;
     constexpr int S = 2 * C2;  // slots per lane
     constexpr int W = L * S;
-    static_assert(S <= 16 && 32 % L == 0 && C2 % 4 == 0, "packed tile shape");
+    static_assert(S <= 16 && 32 % L == 0 && L >= 2 && C2 % 4 == 0, "packed tile shape");
     const int lane = threadIdx.x & 31;
     const int glane = lane % L;
     const int gbase = lane - glane;
     const unsigned gm = group_mask<L>(gbase);
+    const bool bot_lane = glane == 0, top_lane = glane == L - 1;
 
     // Per-group task state (uniform within a group).
     bool active = false, exhausted = false;
@@ -179,24 +216,26 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     Scoring sc{1, -1, -1, 0};
     int64_t sa0 = 0, sb0 = 0;
     int dir = 1;
-    int32_t m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
-    int32_t Q = 0;              // frame offset: thr = T + Q
-    int32_t bkey = 0, bbase = 0, bd = 0;  // best cell: group key, window base i, diagonal
-    int32_t ng = 1;             // |gap|
-    uint32_t ma2 = 0, mi2 = 0;  // packed match / mismatch + 2|gap|
-    bool prev_dead = false, fin = false, want = false;
+    int32_t mn = 0, m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
+    int32_t Q = 0;                      // frame offset: thr = T + Q
+    int32_t kR = 0;                     // rebase step
+    int32_t xup = 0;                    // (x + 1) * 512: a group key this large raises T
+    int32_t bkey = 0, bi0 = 0, bd = 0;  // best cell: group key, this lane's i0, diagonal
+    int32_t ng = 1;                     // |gap|
+    uint32_t ma2 = 0, mi2 = 0;          // packed 16 * (match / mismatch + 2|gap|)
+    bool prev_dead = false, fin = false, rb = false;
     uint32_t E[C2], O[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) { E[t] = kDead2; O[t] = kDead2; }
     uint32_t Aw = 0, LA = 0, Bw = 0, LB = 0;
-    int la_n = 16, lb_n = 16;  // warp-uniform lookahead counters
-    int32_t budget = 0;        // warp-uniform: half-steps known to stay inside every rectangle
+    int la_n = 16;        // warp-uniform: diagonal pairs the lookahead words still cover
+    int32_t budget = 0;   // warp-uniform: diagonal pairs known to stay inside every rectangle
     const int32_t lane_bits = (31 - glane) << 4;
     const uint32_t dead16 = (uint32_t)kDead & 0xFFFFu;
 
     auto retire = [&](bool overflow) {
         if (bd > 0) {
-            bi = bbase + (31 - ((bkey >> 4) & 31)) * S + (S - 1 - (bkey & 15));
+            bi = (bi0 - glane * S) + (31 - ((bkey >> 4) & 31)) * S + (S - 1 - (bkey & 15));
             bj = bd - bi;
         }
         if (glane == 0) src.retire(gj, task, overflow, T, bi, bj);
@@ -204,36 +243,33 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         ng = 0;  // the frame offset stays put while the group waits
     };
 
-    // Half-steps until a cell of this group's window can leave the
-    // rectangle: each half-step moves the top slot's i or the bottom
-    // slot's j up by one (window shifts recompute it).
+    // Diagonal pairs until a cell of this group's window can leave the
+    // rectangle: each pair moves the top slot's i and the bottom slot's j
+    // up by one (window shifts recompute it).
     auto refresh_budget = [&]() {
         const int32_t mg = min(m - (i0 - glane * S + W - 1), n - (j0 + glane * S));
         budget = __reduce_min_sync(FULL, active ? mg : INT32_MAX);
     };
 
-    // One anti-diagonal.  Returns the warp-wide "something to do" vote:
-    // a window edge went live, a task ended, a lookahead word ran out, the
-    // frame needs a rebase, the masking-free budget ran low, or a group
-    // waits for a task.  Everything else is straight-line code.
-    auto half = [&](auto odd_tag, auto masked_tag) -> bool {
+    // One anti-diagonal and the bookkeeping that cannot wait for the end of
+    // the pair: T and the best cell.  Returns the group key (negative iff
+    // every cell of the diagonal was pruned) and the diagonal's threshold.
+    auto diag = [&](auto odd_tag, auto masked_tag, int32_t &thr) -> int32_t {
         constexpr bool ODD = decltype(odd_tag)::value;
         constexpr bool MASKED = decltype(masked_tag)::value;
         ++d;
         Q += ng;
-        --budget;
         if (ODD) {
             ++i0;
             Aw = __funnelshift_r(Aw, LA, 2);
             LA >>= 2;
-            --la_n;
         } else {
             ++j0;
             Bw = __funnelshift_l(LB, Bw, 2);
             LB <<= 2;
-            --lb_n;
         }
-        const uint32_t nthr2 = pack2(-kScale * (T + Q));
+        thr = T + Q;
+        const uint32_t nthr2 = prmt((uint32_t)(-kScale * thr), 0u, 0x1010);
         // rectangle bounds of this lane's slots, clamped into 16 bits (only
         // the masked copy reads them)
         uint32_t lo1_2 = 0, nhi1_2 = 0;
@@ -243,60 +279,83 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             nhi1_2 = pack2(min(max(-hi - 1, -1024), 1024));
         }
         const uint32_t xx = Aw ^ Bw;
-        const uint32_t eq = ~(xx | (xx >> 1)) & 0x55555555u;
+        const uint32_t eq7 = ~(xx | (xx << 1));
         int32_t lkey;
-        uint32_t vedge;
         if (ODD) {
             uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
-            if (glane == L - 1) edge = kDead2;
-            lkey = dp16<C2, true, MASKED>(O, E, edge, eq, ma2, mi2, nthr2, lo1_2, nhi1_2);
-            vedge = __shfl_sync(FULL, O[C2 - 1], L - 1, L) >> 16;
+            if (top_lane) edge = kDead2;
+            lkey = dp16<C2, true, MASKED>(O, E, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2);
         } else {
             uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
-            if (glane == 0) edge = kDead2;
-            lkey = dp16<C2, false, MASKED>(E, O, edge, eq, ma2, mi2, nthr2, lo1_2, nhi1_2);
-            vedge = __shfl_sync(FULL, E[0], 0, L) & 0xFFFFu;
+            if (bot_lane) edge = kDead2;
+            lkey = dp16<C2, false, MASKED>(E, O, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2);
         }
         // Group key: value above lane above slot in lane, so one max finds
         // the lowest window slot among the cells holding the maximum.
         const int32_t mkey = __reduce_max_sync(gm, (lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
-        const int32_t xm = mkey >> 9;  // best r - thr on the diagonal (-1: none live)
-        const bool up = active && xm > sc.x;
-        T = up ? T - sc.x + xm : T;
-        bkey = up ? mkey : bkey;           // decoded at retire
-        bbase = up ? i0 - glane * S : bbase;
-        bd = up ? d : bd;
-        const bool dead = (mkey < 0);
-        fin = active && ((dead && prev_dead) || d >= m + n);
-        prev_dead = dead;
-        want = active && !fin && vedge != dead16;
-        bool ev = want || fin || (ODD ? la_n == 0 : lb_n == 0);
-        if (!ODD) {
-            ev = ev || (active && T + Q + ng >= kRebase) || !active;
-            if (!MASKED) ev = ev || budget < 2;
+        if (mkey >= xup) {  // best value - thr > x: T rises (decoded at retire)
+            T += (mkey >> 9) - sc.x;
+            bkey = mkey;
+            bi0 = i0;
+            bd = d;
         }
+        return mkey;
+    };
+
+    // One pair of anti-diagonals (odd, then even).  Returns the warp-wide
+    // "something to do" vote: a window edge went live, a task ended, the
+    // lookahead words ran out, a frame needs a rebase, the masking-free
+    // budget ran out, or a group waits for a task.
+    auto pair = [&](auto masked_tag) -> bool {
+        constexpr bool MASKED = decltype(masked_tag)::value;
+        int32_t thr_o, thr_e;
+        const int32_t key_o = diag(std::true_type{}, masked_tag, thr_o);
+        const int32_t key_e = diag(std::false_type{}, masked_tag, thr_e);
+        const bool dead_o = key_o < 0, dead_e = key_e < 0;
+        fin = active && ((dead_o && (prev_dead || dead_e)) || d >= mn);
+        prev_dead = dead_e;
+        --budget;
+        --la_n;
+        rb = active && thr_o >= kR;
+        // window edges: this group's bottom lane tests E's bottom slot, its
+        // top lane the top slots of E and O (sign bit set = pruned)
+        const uint32_t ew = top_lane ? (E[C2 - 1] & O[C2 - 1]) : (E[0] << 16);
+        const bool edge = active && (bot_lane || top_lane) && (int32_t)ew >= 0;
+        bool ev = edge || fin || rb || la_n == 0 || (!active && !exhausted);
+        if (!MASKED) ev = ev || budget < 1;
         return __any_sync(FULL, ev);
     };
 
-    // The rare work behind an event.  After an even diagonal, returns true
-    // when the loop must go back to the task switch (a group waits for a
-    // task, no group is left running, or the masking-free budget no longer
-    // covers a diagonal pair).
-    auto handle = [&](const bool odd, const bool masked) -> bool {
+    // The rare work behind an event, after the even diagonal of a pair.
+    // Returns true when the loop must go back to the task switch (a group
+    // waits for a task, no group is left running, the masking-free budget
+    // no longer covers a pair, or, masked, it covers one again).
+    auto handle = [&](const bool masked) -> bool {
         bool ovf = false;
-        if (__any_sync(FULL, want)) {
-            // After an odd diagonal the top slot may seed a cell above the
-            // window, after an even one the bottom slot one below it; with
-            // the opposite edge live too the task goes to a wider tier.
-            const uint32_t vopp = odd ? __shfl_sync(FULL, O[0], 0, L) & 0xFFFFu
-                                      : __shfl_sync(FULL, E[C2 - 1], L - 1, L) >> 16;
-            ovf = want && vopp != dead16;
-            const bool sh = want && !ovf;
-            if (odd) {  // shift up: slot s takes slot s+1
+        const bool go = active && !fin;
+        const bool need_dn_l = bot_lane && live_lo(E[0]);
+        const bool need_up_l = top_lane && (live_hi(E[C2 - 1]) || live_hi(O[C2 - 1]));
+        if (__any_sync(FULL, go && (need_dn_l || need_up_l))) {
+            // Per group: the decision of its bottom and top lanes.
+            const bool blk_up_l = live_lo(E[0]) || live_lo(E[1]) || live_lo(O[0]);
+            const bool blk_dn_l = live_hi(E[C2 - 1]) || live_hi(O[C2 - 1]) ||
+                                  live_hi(E[C2 - 2]) || live_hi(O[C2 - 2]);
+            // every lane takes part in every shuffle (no short-circuit
+            // around a warp-wide collective)
+            const bool up_g = __shfl_sync(FULL, (int)need_up_l, L - 1, L) != 0;
+            const bool dn_g = __shfl_sync(FULL, (int)need_dn_l, 0, L) != 0;
+            const bool bu = __shfl_sync(FULL, (int)blk_up_l, 0, L) != 0;
+            const bool bdn = __shfl_sync(FULL, (int)blk_dn_l, L - 1, L) != 0;
+            const bool nu = go && up_g;
+            const bool nd = go && dn_g;
+            ovf = (nu && bu) || (!nu && nd && bdn);
+            const bool su = nu && !bu;           // shift up: slot s takes slot s+1
+            const bool sd = !nu && nd && !bdn;   // shift down: slot s takes slot s-1
+            if (__any_sync(FULL, su)) {
                 uint32_t ne = __shfl_down_sync(FULL, E[0], 1, L);
                 uint32_t no = __shfl_down_sync(FULL, O[0], 1, L);
-                if (glane == L - 1) { ne = kDead2; no = kDead2; }
-                if (sh) {
+                if (top_lane) { ne = kDead2; no = kDead2; }
+                if (su) {
                     const uint32_t te = prmt(E[0], ne, 0x5432), to = prmt(O[0], no, 0x5432);
 #pragma unroll
                     for (int t = 0; t < C2 - 1; ++t) { E[t] = E[t + 1]; O[t] = O[t + 1]; }
@@ -305,11 +364,12 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                     i0 += 1;
                     j0 -= 1;
                 }
-            } else {    // shift down: slot s takes slot s-1
+            }
+            if (__any_sync(FULL, sd)) {
                 uint32_t pe = __shfl_up_sync(FULL, E[C2 - 1], 1, L);
                 uint32_t po = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
-                if (glane == 0) { pe = kDead2; po = kDead2; }
-                if (sh) {
+                if (bot_lane) { pe = kDead2; po = kDead2; }
+                if (sd) {
                     const uint32_t te = prmt(pe, E[C2 - 1], 0x5432);
                     const uint32_t to = prmt(po, O[C2 - 1], 0x5432);
 #pragma unroll
@@ -320,7 +380,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                     j0 += 1;
                 }
             }
-            if (sh) {
+            if (su || sd) {
                 Aw = fwd16_u(pk, nw, sa0, dir, i0);
                 LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
                 Bw = back16_u(pk, nw, sb0, dir, j0);
@@ -329,36 +389,38 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             fin = fin || ovf;
         }
         if (fin) retire(ovf);
-        if (la_n == 0) {
+        const bool refill = la_n == 0;
+        if (refill) {
             LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+            LB = back16_u(pk, nw, sb0, dir, j0 + 16);
             la_n = 16;
         }
-        if (lb_n == 0) {
-            LB = back16_u(pk, nw, sb0, dir, j0 + 16);
-            lb_n = 16;
-        }
-        if (odd) {
-            if (!masked) refresh_budget();
-            return false;
-        }
-        // Keep thr = T + Q of the next diagonal below 2 * kRebase (see the
-        // header comment): rebase once it would reach kRebase.
-        const bool rb = active && T + Q + ng >= kRebase;
-        if (rb) {
-            const uint32_t mr = pack2(-kScale * kRebase);
+        // Every live value of the pair is >= 16 thr of its odd diagonal:
+        // once that threshold reaches kR, take kR off the frame.
+        if (active && rb) {
+            const uint32_t mr = pack2(-kScale * kR);
 #pragma unroll
             for (int t = 0; t < C2; ++t) {
                 E[t] = __viaddmax_s16x2(E[t], mr, kDead2);
                 O[t] = __viaddmax_s16x2(O[t], mr, kDead2);
             }
-            Q -= kRebase;
+            Q -= kR;
         }
-        if (!masked) refresh_budget();
         if constexpr (Src::kCanAbort) {
             if (__any_sync(FULL, src.aborted())) return true;
         }
-        return __any_sync(FULL, !active && !exhausted) || !__any_sync(FULL, active) ||
-               (!masked && budget < 2);
+        if (__any_sync(FULL, !active && !exhausted) || !__any_sync(FULL, active)) return true;
+        if (!masked) {
+            refresh_budget();
+            return budget < 1;
+        }
+        // Masked pairs are dearer: look again every 16 pairs (with the
+        // refill) and go back to the unmasked copy once it is safe.
+        if (refill) {
+            refresh_budget();
+            return budget >= 1;
+        }
+        return false;
     };
 
     using T0 = std::integral_constant<bool, false>;
@@ -388,7 +450,10 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         dir = e.A.dir;
                         m = e.m;
                         n = e.n;
+                        mn = m + n;
                         ng = -sc.gap;
+                        kR = rebase_step16(sc);
+                        xup = (sc.x + 1) * 512;
                         ma2 = pack2(kScale * (sc.match + 2 * ng));
                         mi2 = pack2(kScale * (sc.mismatch + 2 * ng));
                         // origin (H = 0) at window slot W/2, stored as 16 * (0 + x)
@@ -424,15 +489,13 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             continue;
         }
         refresh_budget();
-        if (budget >= 2) {
+        if (budget >= 1) {
             for (;;) {  // no cell of any window can leave its rectangle
-                if (half(T1{}, T0{})) handle(true, false);
-                if (half(T0{}, T0{}) && handle(false, false)) break;
+                if (pair(T0{}) && handle(false)) break;
             }
         } else {
             for (;;) {
-                if (half(T1{}, T1{})) handle(true, true);
-                if (half(T0{}, T1{}) && handle(false, true)) break;
+                if (pair(T1{}) && handle(true)) break;
             }
         }
     }
@@ -470,6 +533,7 @@ serve16_kernel(ServeArgs a, const uint32_t *pk, int64_t nw)
         lockstep_loop<L2, C2>(help, pk, nw);
         if (__any_sync(FULL, help.failed || help.aborted())) break;
     }
+    __threadfence();  // this warp's queue pushes before it counts itself out
     if ((threadIdx.x & 31) == 0) atomicSub(&a.ctl->ring_alive, 1u);
 }
 

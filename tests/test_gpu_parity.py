@@ -133,7 +133,7 @@ def test_every_first_tile(X, orc, tile):
 
 PACKED_LIMIT_SCORINGS = [
     (64, -128, -64, 1472),  # every limit at once: the frame is rebased every diagonal pair
-    (1, -128, -1, 1535),    # largest x
+    (1, -2, -1, 1535),      # largest x, mismatch = 2 gap
     (3, -2, -125, 100),     # gap-dominated frame growth
     (127, -1, -1, 1409),    # largest match
     (1, 0, -1, 50),         # mismatch + 2|gap| > 0
@@ -158,7 +158,8 @@ def test_packed_tiles_at_their_limits(X, orc, tile, scores):
 
 
 @pytest.mark.parametrize("scores", [(1, -1, -1, 1536), (128, -1, -1, 10), (1, -129, -1, 10),
-                                    (1, -1, -128, 10)], ids=lambda s: "_".join(map(str, s)))
+                                    (1, -1, -128, 10), (1, -128, -1, 1535), (2, -3, -1, 30)],
+                         ids=lambda s: "_".join(map(str, s)))
 def test_packed_tile_falls_back_outside_its_range(X, orc, scores):
     """A forced packed tile runs the 32-bit tile of its shape when the
     scoring does not fit 16 bits, with the same results."""
