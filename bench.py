@@ -66,8 +66,8 @@ def parse():
                     help="seed discovery only: reliable 31-mers and candidate pairs at 29x")
     ap.add_argument("--seeds-genome", type=int, default=4_600_000,
                     help="genome length of the seed-discovery read set")
-    ap.add_argument("--seeds-rowwise", action="store_true",
-                    help="seed discovery with the row-wise product")
+    ap.add_argument("--seeds-sort", action="store_true",
+                    help="seed discovery with the sort-based product (default: row-wise)")
     ap.add_argument("--no-seeds", action="store_true",
                     help="skip the seed-discovery object of the default line")
     ap.add_argument("--seeds-cpu", action="store_true",
@@ -369,19 +369,26 @@ def run_ours(args):
     value = ws * cells / (mean_ms * 1e-3) / 1e9
     pairs_s = ws * w.n_pairs / (mean_ms * 1e-3)
 
-    # plain per-10,000-pair form, same inputs
+    # plain per-10,000-pair form, same inputs, same first tile and arithmetic
     plain = None
     if not args.no_plain:
         pal = X.Aligner(device=local, mode=X.XDROP_MODE_PLAIN)
+        pal.set_tile(*batched.tile())
         pstream = torch.cuda.ExternalStream(pal.stream(), device=dev_name)
         for _ in range(2):
             step(pal, pstream)
         pms = [step(pal, pstream)[0] for _ in range(max(2, min(args.steps, 3)))]
         assert (dev.results() == res).all()
         pm = statistics.mean(pms)
+        pt = pal.tile()
+        assert pt == batched.tile()
         plain = {"value": cells / (pm * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pm,
-                 "pairs_per_s": w.n_pairs / (pm * 1e-3), "tile": "32 lanes x 4 cells",
-                 "launch": "one launch per 10,000-pair sub-batch"}
+                 "pairs_per_s": w.n_pairs / (pm * 1e-3),
+                 "tile": f"{pt[0]} lanes x {pt[1] & 0xff} cells"
+                         + (" (16-bit packed)" if pt[1] & X.XDROP_TILE_PACKED16 else "")
+                         + ", the batched form's first tile",
+                 "launch": "one launch of the first tile per 10,000-pair sub-batch in pair "
+                           "order (no binning, no graph, no autotuning), then the same wider tiers"}
         pal.close()
 
     # end to end through the host-memory call (pinned host buffers)
@@ -410,7 +417,8 @@ def run_ours(args):
                "d2h_bytes_per_step": int(hout.nbytes), "pairs_per_s": ws * w.n_pairs / em,
                "ms_per_step": em * 1e3, "call": "xdrop_submit + xdrop_sync (host buffers)"}
 
-    # roofline of the dominant kernel: first-tier persistent band kernel
+    # roofline of the dominant kernel: first-tier persistent band kernel,
+    # against the int32 issue limit (SMs x 128 lanes x clock)
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
@@ -419,21 +427,24 @@ def run_ours(args):
     tile = batched.tile()
     packed = bool(tile[1] & X.XDROP_TILE_PACKED16)
     cpl = tile[1] & 0xff
-    if packed:  # 16-bit cells, two per lane op: the issue limit counts 2 ops per lane
-        kname, op_unit, per_lane = f"lockstep16_kernel<{tile[0]},{cpl // 2}>", "Tint16op/s", 2
-        peak *= 2
+    if packed:
+        kname = f"lockstep16_kernel<{tile[0]},{cpl // 2}>"
     else:
-        kname, op_unit, per_lane = f"lockstep_kernel<{tile[0]},{cpl}>", "Tint32op/s", 1
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": op_unit,
+        kname = f"lockstep_kernel<{tile[0]},{cpl}>"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tintop/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic_from_profile(kname),
             "kernel": kname,
             "kernel_ms": main_mean,
-            "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} lanes/clk x "
-                          f"{per_lane} op per lane x {sm_max:.0f} MHz (max SM clock)",
+            "tcups": (cells_tier0 / (main_mean * 1e-3) / 1e12) if main_mean else None,
+            "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes/clk "
+                          f"x {sm_max:.0f} MHz (max SM clock): the int32 issue limit",
             "ops_per_cell": INT_OPS_PER_CELL, "cells_in_kernel": cells_tier0,
             "step_frac": INT_OPS_PER_CELL * cells / (mean_ms * 1e-3) / 1e12 / peak,
-            "packed16": packed}
+            "packed16": packed,
+            # each packed lane op does two 16-bit cells: against twice the
+            # int32 issue limit the same kernel reads as this fraction
+            "frac_int16x2_issue": (achieved / (2 * peak)) if (achieved and packed) else None}
 
     serving_runs = None
     if not args.no_serve:
@@ -506,15 +517,17 @@ def run_serve_sweep(args):
 
 def seed_discovery_runs(genome=1_000_000, timeout_s=240):
     """Seed discovery (the upstream row: reliable 31-mers and candidate
-    pairs) beside the headline: both products on 29x reads of a genome of
-    `genome` bases, each timed by `bench.py --seeds` in a process of its
-    own, so that nothing there can touch the alignment numbers above.  A
-    failed run is reported, not raised."""
+    pairs) beside the headline: both products (row-wise, the default, and
+    sort-based) on 29x reads of a genome of `genome` bases, each timed by
+    `bench.py --seeds` in a process of its own, so that nothing there can
+    touch the alignment numbers above.  A failed run is reported, not
+    raised."""
     out = {"workload": f"reads-29x-genome{genome}-err1pct, k=31, window [20, 50]",
            "timing": "CUDA events around the library's pipeline, median of 3 steps"}
     keep = ("value", "unit", "ms_per_step", "host_ms_per_step", "product", "candidates",
-            "reverse_strand", "candidates_sha256", "occurrences", "reads", "cpu_baseline")
-    for name, extra in (("sort", ["--seeds-cpu"]), ("rowwise", ["--seeds-rowwise"])):
+            "reverse_strand", "candidates_sha256", "occurrences", "nonzeros", "reads",
+            "cpu_baseline", "roofline")
+    for name, extra in (("rowwise", ["--seeds-cpu"]), ("sort", ["--seeds-sort"])):
         cmd = [sys.executable, os.path.abspath(__file__), "--seeds", "--seeds-genome", str(genome),
                "--steps", "3", "--warmup", "1"] + extra
         try:
@@ -529,17 +542,36 @@ def seed_discovery_runs(genome=1_000_000, timeout_s=240):
         else:
             tail = (r.stderr.strip().splitlines() or ["(no output)"])[-1]
             out[name] = {"error": f"exit {r.returncode}: {tail[:300]}"}
-    digests = [out[n].get("candidates_sha256") for n in ("sort", "rowwise")]
+    digests = [out[n].get("candidates_sha256") for n in ("rowwise", "sort")]
     out["products_agree"] = (digests[0] == digests[1]) if all(digests) else None
     return out
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth of the GB300s, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback: 6.8 TB/s, one earlier GB300 copy measurement"
+
+
+def seed_algorithmic_bytes(read_set_bytes, occurrences, nonzeros, candidates):
+    """Bytes seed discovery must move by its method: the packed read set
+    read once, every k-mer occurrence's 64-bit code written once and read
+    once, every nonzero of the read-by-k-mer matrix A written once and read
+    once (8 B each way), and the candidate records (20 B pair + 4 B count)
+    written once."""
+    return read_set_bytes + 16 * occurrences + 16 * nonzeros + 24 * candidates
 
 
 def run_seeds(args):
     """Seed discovery at the paper's parameters (k = 31, stride 1, frequency
     window [20, 50]) on 29x coverage of a random genome of --seeds-genome
     bases, reads of mean 10 kb with 1 % errors from both strands.  One step
-    = one xdrop_find_candidates over the resident reads (the sort-based
-    product, or the row-wise one with --seeds-rowwise), timed with the CUDA
+    = one xdrop_find_candidates over the resident reads (the row-wise
+    product, or the sort-based one with --seeds-sort), timed with the CUDA
     events the library records around its pipeline (the candidates' copy to
     host included) and, beside it, on the host around the synchronous call;
     reloading the reads between steps, outside the timed region, drops the
@@ -559,7 +591,7 @@ def run_seeds(args):
         for step in range(args.warmup + args.steps):
             X.xdrop_load_reads(al.ctx, packed, off, lens)
             t0 = time.perf_counter()
-            pairs, shared = X.xdrop_find_candidates(al.ctx, k, lo, hi, 1, args.seeds_rowwise)
+            pairs, shared = X.xdrop_find_candidates(al.ctx, k, lo, hi, 1, not args.seeds_sort)
             dt = time.perf_counter() - t0
             st = X.xdrop_get_seed_stats(al.ctx)
             if step >= args.warmup:
@@ -580,6 +612,17 @@ def run_seeds(args):
                "sample": f"29x reads of a {g}-base genome, 1% errors ({s_occ} occurrences), "
                          f"one call, {dt:.1f} s"}
     names = {X.XDROP_SEEDS_SORT: "sort", X.XDROP_SEEDS_ROWWISE: "rowwise"}
+    nnz = int(st["nonzeros"])
+    roof = None
+    if nnz:  # the row-wise product ran and counted A's nonzeros
+        alg = seed_algorithmic_bytes(int(packed.nbytes), n_occ, nnz, len(pairs))
+        peak, basis = hbm_peak_gbs()
+        gbs = alg / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": None, "algorithmic_bytes": alg, "peak_basis": basis,
+                "bytes_basis": "2-bit read set read once + 16 B per k-mer occurrence (its 64-bit "
+                               "code written once and read once) + 16 B per nonzero of A "
+                               "(written once, read once) + 24 B per candidate record"}
     print(json.dumps({"metric": f"seed discovery, k-mer occurrences/s (k={k}, window [{lo}, {hi}])",
                       "value": n_occ / (ms * 1e-3), "unit": "occurrences/s", "ms_per_step": ms,
                       "host_ms_per_step": statistics.median(host), "steps": args.steps,
@@ -589,7 +632,8 @@ def run_seeds(args):
                       "candidates_sha256": hashlib.sha256(pairs.tobytes() + shared.tobytes())
                       .hexdigest()[:16],
                       "cpu_baseline": cpu,
-                      "reads": int(len(lens)), "occurrences": n_occ, "data": "synthetic",
+                      "reads": int(len(lens)), "occurrences": n_occ, "nonzeros": nnz,
+                      "roofline": roof, "data": "synthetic",
                       "config": {"workload": f"reads-29x-genome{args.seeds_genome}-err1pct",
                                  "timing": "CUDA events around the library's pipeline"}}),
           flush=True)

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -113,6 +114,7 @@ struct xdrop_ctx {
     Job *d_job = nullptr;
     uint32_t *d_ctrs = nullptr;
     DevBuf order, spill[3], wide;
+    DevBuf plain_ctl;  // plain mode: task count and work counter per sub-batch
     size_t cap_tasks = 0;
     int64_t wide_per_cta = 0;
     int wide_grid = 0;
@@ -124,7 +126,9 @@ struct xdrop_ctx {
     Tile tile0 = {8, 8};
     int tile0_bps = 0;            // resident blocks per SM of tile0
     Tile forced = {0, 0};         // xdrop_set_tile
-    std::map<std::tuple<int, int, int, int>, Tile> tuned;  // per scoring
+    // tuned first tile per (scoring, length bucket of the job)
+    std::map<std::tuple<int, int, int, int, int>, Tile> tuned;
+    DevBuf tune_pairs, tune_out;  // autotuning sample and its results
     uint64_t scratch_version = 0; // bumped whenever a scratch buffer moves
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev_main0 = nullptr, ev_main1 = nullptr;  // recorded inside the graph
@@ -142,6 +146,7 @@ struct xdrop_ctx {
     bool have_reads = false;
     uint64_t reads_gen = 0;  // bumped by every xdrop_load_reads
     xd::Server *srv = nullptr;
+    uint64_t serve_idle_ns = 0;  // xdrop_set_serve_idle (0: the default)
 
     // the last seed discovery result (xdrop_find_candidates)
     std::vector<Pair> cand_pairs;
@@ -267,7 +272,7 @@ const Tile kPackedTiles[] = {{4, 8, true},  {2, 16, true}, {4, 16, true},
 int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out);
 
 // Time the whole batched sequence for every candidate first tile on a
-// sample of `job` (its first pairs), pick the fastest.  Synchronous.
+// sample of `job`, pick the fastest.  Synchronous.
 int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
 {
     cudaStream_t s = c->stream;
@@ -275,11 +280,22 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     // faster than the 32-bit tile of its shape), on a third of the job so
     // the end of the sample, where few extensions are left, does not decide
     // between tiles of different concurrency; other scorings time the
-    // 32-bit tiles on an eighth.
+    // 32-bit tiles on an eighth.  The sample is stratified and random (one
+    // pair out of every block of 3 or 8, seeded), so it has the job's
+    // length mix even when the input is sorted or clustered.
     const bool packed = packed_scoring_ok(job.sc);
+    const uint32_t stride = job.n_pairs <= 3 * 4096 ? 1u : (packed ? 3u : 8u);
+    const uint64_t m = (job.n_pairs + stride - 1) / stride;
+    int rc0;
+    if ((rc0 = dev_alloc(c, c->tune_pairs, std::max<uint64_t>(m, 1) * sizeof(Pair)))) return rc0;
+    if ((rc0 = dev_alloc(c, c->tune_out, std::max<uint64_t>(m, 1) * sizeof(xdrop_result))))
+        return rc0;
+    CK(launch_sample_pairs(job.pairs, job.n_pairs, stride, 0x5eed1234u, (Pair *)c->tune_pairs.p, m,
+                           s));
     Job js = job;
-    js.n_pairs = std::min<uint64_t>(job.n_pairs,
-                                    std::max<uint64_t>(4096, job.n_pairs / (packed ? 3 : 8)));
+    js.pairs = (const Pair *)c->tune_pairs.p;
+    js.out = (int32_t *)c->tune_out.p;
+    js.n_pairs = m;
     CK(cudaStreamSynchronize(s));
     *tk->h_job = js;
     CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
@@ -316,6 +332,30 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     return best->lanes ? XDROP_OK : fail(XDROP_ECUDA, "no tile could be timed");
 }
 
+// Length bucket of a job (the tuning key beside the scoring): the length
+// bin ceil(log2(max(m, n) + 1)) holding the median of the job's work, each
+// task weighted by 2^bin (about its length), from a device histogram read
+// back synchronously.  Workloads of different length mixes tune apart.
+int length_bucket(xdrop_ctx *c, Ticket *tk, int *bucket)
+{
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->d_ctrs + C_HIST, 0, 32 * 4, s));
+    CK(launch_length_hist(c->d_job, c->sm_count * 4, c->d_ctrs + C_HIST, s));
+    CK(cudaMemcpyAsync(tk->h_ctrs, c->d_ctrs + C_HIST, 32 * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double total = 0, run = 0;
+    for (int b = 0; b < 32; ++b) total += (double)tk->h_ctrs[b] * std::ldexp(1.0, b);
+    *bucket = 0;
+    for (int b = 0; b < 32; ++b) {
+        run += (double)tk->h_ctrs[b] * std::ldexp(1.0, b);
+        if (run * 2 >= total && total > 0) {
+            *bucket = b;
+            break;
+        }
+    }
+    return XDROP_OK;
+}
+
 int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out)
 {
     Tile t = c->forced;
@@ -324,7 +364,9 @@ int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out)
         *out = t;
         return XDROP_OK;
     }
-    auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x);
+    int bucket = 0;
+    if (int rc = length_bucket(c, tk, &bucket)) return rc;
+    auto key = std::make_tuple(job.sc.match, job.sc.mismatch, job.sc.gap, job.sc.x, bucket);
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) {
         *out = it->second;
@@ -369,19 +411,47 @@ int run_batched(xdrop_ctx *c, Ticket *tk)
     return XDROP_OK;
 }
 
-int run_plain(xdrop_ctx *c, Ticket *tk, uint64_t n_pairs)
+// Plain form (Section "Method", Baseline: batches of 10,000 alignments, each
+// sent to the GPU on its own): one launch of the first band tile per
+// 10,000-pair sub-batch, in pair order, with a grid sized to the
+// sub-batch; no length binning, no graph, no autotuning.  The tile is the
+// forced one (xdrop_set_tile), else packed 4x16, so that it can run the
+// very tile and arithmetic of the batched form.  Overflowing extensions go
+// through the same wider tiers afterwards.
+int run_plain(xdrop_ctx *c, Ticket *tk, const Job &job)
 {
     cudaStream_t s = c->stream;
+    const uint64_t n_pairs = job.n_pairs;
     CK(cudaMemsetAsync(c->d_ctrs, 0, C_NBAD * 4, s));
-    for (uint64_t p0 = 0; p0 < n_pairs; p0 += kSubBatchPairs) {
-        uint64_t np = std::min(kSubBatchPairs, n_pairs - p0);
-        CK(launch_window(Tile{32, 4}, false, c->d_job, (uint32_t)(2 * p0), (uint32_t)(2 * np),
-                         spill_of(c, 0), s));
+    Tile t0 = c->forced.lanes ? c->forced : Tile{4, 16, true};
+    if (t0.packed && !packed_scoring_ok(job.sc)) t0.packed = false;
+    c->tile0 = t0;
+    const int bps = persistent_blocks_per_sm(t0);
+    if (bps <= 0) return fail(XDROP_ECUDA, "tile %dx%d not available", t0.lanes, t0.c);
+    const uint64_t n_sub = (n_pairs + kSubBatchPairs - 1) / kSubBatchPairs;
+    int rc;
+    if ((rc = dev_alloc(c, c->plain_ctl, n_sub * 8))) return rc;
+    uint32_t *order = (uint32_t *)c->order.p, *ctl = (uint32_t *)c->plain_ctl.p;
+    CK(launch_plain_setup(n_pairs, kSubBatchPairs, order, ctl, s));
+    const uint64_t groups_per_block = 256 / t0.lanes;
+    for (uint64_t k = 0; k < n_sub; ++k) {
+        const uint64_t p0 = k * kSubBatchPairs, np = std::min(kSubBatchPairs, n_pairs - p0);
+        const uint64_t blocks = (2 * np + groups_per_block - 1) / groups_per_block;
+        const int grid = (int)std::min<uint64_t>(blocks, (uint64_t)c->sm_count * bps);
+        CK(launch_persistent(t0, grid, c->d_job, order + 2 * p0, ctl + 2 * k, ctl + 2 * k + 1,
+                             spill_of(c, 0), s));
+    }
+    tk->launches += (uint32_t)(1 + n_sub);
+    Tile t1 = next_tile_after(t0);
+    int k = 0;
+    if (t1.width() < 512) {
+        CK(launch_spill(t1, false, c->sm_count * 4, c->d_job, spill_of(c, 0), spill_of(c, 1), s));
+        k = 1;
         tk->launches += 1;
     }
-    CK(launch_spill(Tile{32, 16}, false, c->sm_count * 2, c->d_job, spill_of(c, 0),
-                    spill_of(c, 1), s));
-    CK(launch_wide(false, c->wide_grid, c->d_job, spill_of(c, 1), (int32_t *)c->wide.p,
+    CK(launch_spill(Tile{32, 16}, false, c->sm_count * 2, c->d_job, spill_of(c, k),
+                    spill_of(c, k + 1), s));
+    CK(launch_wide(false, c->wide_grid, c->d_job, spill_of(c, k + 1), (int32_t *)c->wide.p,
                    c->wide_per_cta, s));
     tk->launches += 2;
     return XDROP_OK;
@@ -418,7 +488,7 @@ int launch_ticket(xdrop_ctx *c, Ticket *tk, const Job &job, uint32_t maxlen)
         if ((rc = pick_tile(c, tk, job, &c->tile0))) return rc;
     }
     if (job.n_pairs) {
-        if (c->mode == XDROP_MODE_PLAIN) rc = run_plain(c, tk, job.n_pairs);
+        if (c->mode == XDROP_MODE_PLAIN) rc = run_plain(c, tk, job);
         else rc = run_batched(c, tk);
         if (rc) return rc;
     }
@@ -723,14 +793,12 @@ int xdrop_sync(xdrop_ctx *c, xdrop_ticket t, int64_t timeout_ns)
     st.main_kernel_ms = ms_main;
     st.tasks = 2 * (uint64_t)tk->n_pairs;
     st.overflow_tasks = tk->h_ctrs[C_SPILL0];
-    st.wide_tasks = (c->mode == XDROP_MODE_PLAIN || next_tile_after(c->tile0).width() >= 512)
-                        ? tk->h_ctrs[C_SPILL1] : tk->h_ctrs[C_SPILL2];
+    st.wide_tasks = next_tile_after(c->tile0).width() >= 512 ? tk->h_ctrs[C_SPILL1]
+                                                              : tk->h_ctrs[C_SPILL2];
     st.launches = tk->launches;
     st.graph_replays = tk->graph_replays;
-    st.tile_lanes = c->mode == XDROP_MODE_PLAIN ? 32 : c->tile0.lanes;
-    st.tile_cells = c->mode == XDROP_MODE_PLAIN
-                        ? 4
-                        : c->tile0.c | (c->tile0.packed ? XDROP_TILE_PACKED16 : 0);
+    st.tile_lanes = c->tile0.lanes;
+    st.tile_cells = c->tile0.c | (c->tile0.packed ? XDROP_TILE_PACKED16 : 0);
     c->last = st;
     const uint32_t nbad = tk->device_submit ? tk->h_ctrs[C_NBAD] : 0;
     free_ticket(c, tk);
@@ -753,6 +821,9 @@ void xdrop_free(xdrop_ctx *c)
     if (c->ev_main0) cudaEventDestroy(c->ev_main0);
     if (c->ev_main1) cudaEventDestroy(c->ev_main1);
     cudaFree(c->order.p);
+    cudaFree(c->plain_ctl.p);
+    cudaFree(c->tune_pairs.p);
+    cudaFree(c->tune_out.p);
     for (auto &s : c->spill) cudaFree(s.p);
     cudaFree(c->wide.p);
     cudaFree(c->d_job);
@@ -835,7 +906,8 @@ int xdrop_load_reads(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_
         // not fit 16 bits run on the serving kernel's 32-bit second tier.
         const Tile t = c->forced.lanes ? c->forced : Tile{4, 16, true};
         c->srv = xd::server_create(c->device, c->sm_count, c->budget, t, rr, c->h_len.data(),
-                                   (int32_t *)c->wide.p, c->wide_per_cta, c->wide_grid, err);
+                                   (int32_t *)c->wide.p, c->wide_per_cta, c->wide_grid,
+                                   c->serve_idle_ns, err);
         if (!c->srv) return fail(XDROP_ECUDA, "%s", err.c_str());
     }
     return XDROP_OK;
@@ -986,7 +1058,17 @@ int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st)
         st->spill_reserved = s.spill_reserved;
         st->spill_taken = s.spill_taken;
         st->ring_warps = s.ring_warps;
+        st->idle_exits = s.idle_exits;
     }
+    return XDROP_OK;
+}
+
+int xdrop_set_serve_idle(xdrop_ctx *c, uint64_t idle_ns)
+{
+    if (!c) return fail(XDROP_EINVAL, "context is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->serve_idle_ns = idle_ns;
+    if (c->srv) xd::server_set_idle_ns(c->srv, idle_ns);
     return XDROP_OK;
 }
 
@@ -997,7 +1079,7 @@ int xdrop_find_candidates(xdrop_ctx *c, const xdrop_kmer_params *p, xdrop_pair *
     if (!p || !n || (cap && !pairs)) return fail(XDROP_EINVAL, "NULL argument");
     if (p->k < 1 || p->k > xs::kMaxK || p->stride < 1 || p->lo < 1 || p->lo > p->hi ||
         p->hi > xs::kMaxHi ||
-        (p->flags & ~XDROP_SEEDS_ROWWISE))
+        (p->flags & ~XDROP_SEEDS_SORT))
         return fail(XDROP_EINVAL,
                     "k-mer parameters out of range (k %u, stride %u, lo %u, hi %u, flags %u)", p->k,
                     p->stride, p->lo, p->hi, p->flags);
@@ -1054,6 +1136,8 @@ int xdrop_get_seed_stats(xdrop_ctx *c, xdrop_seed_stats *st)
     st->runs = c->seed_stats.runs;
     st->candidates = c->seed_stats.candidates;
     st->product = c->seed_stats.product;
+    st->pad = 0;
+    st->nonzeros = c->seed_stats.nonzeros;
     return XDROP_OK;
 }
 

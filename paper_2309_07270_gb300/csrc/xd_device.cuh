@@ -912,7 +912,12 @@ struct RingSrc {
                     } else if (cons >= pub) {  // nothing published to take
                         const unsigned long long now = globaltimer_ns();
                         if (idle_since == 0) idle_since = now;
-                        if (v->stop || now - idle_since > v->idle_ns) status = -1;
+                        if (v->stop) {
+                            status = -1;
+                        } else if (now - idle_since > v->idle_ns) {
+                            status = -1;  // hang guard: counted for the host
+                            atomicAdd(&a.ctl->idle_exits, 1u);
+                        }
                         backoff = 1 << level;
                         if (level < 6) ++level;
                     }
@@ -1003,6 +1008,12 @@ struct SpillSrc {
                 --backoff;
             } else {
                 volatile ServeCtl *v = a.ctl;
+                // ring_alive before the queue ends: a ring warp pushes all
+                // its entries and fences before it counts itself out, so
+                // once none is left the tail read after the fence holds
+                // every entry there will ever be
+                const unsigned int alive = v->ring_alive;
+                __threadfence();
                 const unsigned long long tail = *(volatile unsigned long long *)&a.ctl->spill_tail;
                 unsigned long long head = *(volatile unsigned long long *)&a.ctl->spill_head;
                 const unsigned long long want = (unsigned long long)__popc(needm);
@@ -1019,7 +1030,7 @@ struct SpillSrc {
                 }
                 if (status == 1) {
                     level = 0;
-                } else if (head >= tail && (dynamic || v->ring_alive == 0)) {
+                } else if (head >= tail && (dynamic || alive == 0)) {
                     status = -1;
                 } else if (!dynamic) {
                     backoff = 1 << level;
@@ -1109,6 +1120,7 @@ serve_kernel(ServeArgs a, const uint32_t *pk, int64_t nw)
         lockstep_loop<L2, C2>(help, pk, nw);
         if (__any_sync(FULL, help.failed || help.aborted())) break;
     }
+    __threadfence();  // this warp's queue pushes before it counts itself out
     if ((threadIdx.x & 31) == 0) atomicSub(&a.ctl->ring_alive, 1u);
 }
 

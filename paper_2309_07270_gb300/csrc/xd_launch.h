@@ -46,6 +46,17 @@ cudaError_t launch_validate(const Job *jp, uint64_t n_pairs, uint32_t *n_bad, cu
 cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *hist,
                            uint32_t *offs, uint32_t *n_valid, uint32_t *order,
                            cudaStream_t s);
+// Task length histogram of a job: hist[b] += tasks with
+// ceil(log2(max(m, n) + 1)) = b (32 bins, invalid pairs left out).
+cudaError_t launch_length_hist(const Job *jp, int grid, uint32_t *hist, cudaStream_t s);
+// Stratified random sample of a pair table: dst[j] is one pair of the block
+// [j*stride, (j+1)*stride), chosen by a hash of j and seed; m blocks.
+cudaError_t launch_sample_pairs(const Pair *src, uint64_t n, uint32_t stride, uint32_t seed,
+                                Pair *dst, uint64_t m, cudaStream_t s);
+// Plain form: identity task order and per-sub-batch task counts / counters
+// (ctl, 2 words per sub-batch of sub_pairs pairs).
+cudaError_t launch_plain_setup(uint64_t n_pairs, uint64_t sub_pairs, uint32_t *order, uint32_t *ctl,
+                              cudaStream_t s);
 // Reverse complement of every read of `pk` (n_words words) into `out`, at
 // the same offsets (reverse-strand pairs).
 cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *read_off,
@@ -56,14 +67,15 @@ cudaError_t launch_best_seeds(const Pair *pairs, const int32_t *results, uint64_
                               uint32_t *best, cudaStream_t s);
 // Seed discovery over a read set on the device (xd_seeds.cu): the candidate
 // pairs and their shared-k-mer counts, in (a, b) order, into host vectors.
-// flags: XDROP_SEEDS_ROWWISE selects the row-wise product.  Synchronous on
+// flags: XDROP_SEEDS_SORT selects the sort-based product (row-wise otherwise).  Synchronous on
 // `s`.  Returns an XDROP_* code, with a message in err.
 struct SeedStats {
     double ms = 0;              // CUDA events, first kernel to the last copy
     uint64_t occurrences = 0;   // k-mer occurrences
     uint64_t runs = 0;          // k-mers seen at least twice
     uint64_t candidates = 0;
-    uint32_t product = 0;       // XDROP_SEEDS_SORT or XDROP_SEEDS_ROWWISE: the one that ran
+    uint32_t product = 0;       // XDROP_SEEDS_ROWWISE or XDROP_SEEDS_SORT: the one that ran
+    uint64_t nonzeros = 0;      // A's nonzeros, counted by the row-wise product
 };
 int find_candidates(cudaStream_t s, int sm_count, size_t budget, const uint32_t *packed,
                     const uint64_t *read_off, const uint32_t *read_len, uint32_t n_reads,

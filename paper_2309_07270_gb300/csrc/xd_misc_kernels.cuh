@@ -105,6 +105,49 @@ bin_scatter_kernel(const Job *jp, uint32_t *offs, uint32_t *order)
 }
 
 // Largest read length (for sizing the unbounded tier's scratch).
+// Autotuning sample: one pair from every block of `stride` consecutive
+// pairs, at an offset inside the block drawn from a hash of the block index
+// and the seed (a stratified random sample that spans the whole job, so a
+// sorted or clustered input is sampled evenly).
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void sample_pairs_kernel(const Pair *src, uint64_t n, uint32_t stride, uint32_t seed,
+                                    Pair *dst, uint64_t m)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b0 = j * stride;
+        const uint64_t len = (n - b0 < stride) ? n - b0 : stride;
+        dst[j] = src[b0 + mix32((uint32_t)j * 0x9e3779b9u ^ seed) % len];
+    }
+}
+
+// Plain form: the identity task order (tasks in pair order) and, for every
+// sub-batch k of sub_pairs pairs, its task count (ctl[2k]) and a zeroed
+// work counter (ctl[2k + 1]) for its first-tier launch.
+__global__ void plain_setup_kernel(uint64_t n_pairs, uint64_t sub_pairs, uint32_t *order,
+                                   uint32_t *ctl)
+{
+    const uint64_t n_tasks = 2 * n_pairs, n_sub = (n_pairs + sub_pairs - 1) / sub_pairs;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_tasks;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        order[i] = (uint32_t)i;
+        if (i < n_sub) {
+            const uint64_t left = n_pairs - i * sub_pairs;
+            ctl[2 * i] = (uint32_t)(2 * (left < sub_pairs ? left : sub_pairs));
+            ctl[2 * i + 1] = 0;
+        }
+    }
+}
+
 __global__ void max_len_kernel(const uint32_t *read_len, uint32_t n_reads, uint32_t *out)
 {
     uint32_t m = 0;

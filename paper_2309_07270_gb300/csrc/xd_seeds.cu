@@ -10,10 +10,11 @@
 //      each k-mer's occurrences become one run, in read and position order;
 //   3. the runs of length >= 2 (run-length encoding).
 // Then A * A^T, A the read-by-reliable-k-mer matrix, one of two ways:
-//   sort-based (default): count_kernel and emit_kernel write one entry per
-//      (read pair, shared reliable k-mer); a radix sort by pair, a gather
-//      and a reduce-by-key with xs::CandMerge give one candidate per pair;
-//   row-wise (XDROP_SEEDS_ROWWISE): A's columns (csc_kernel) and rows
+//   sort-based (XDROP_SEEDS_SORT): count_kernel and emit_kernel write one
+//      entry per (read pair, shared reliable k-mer); a radix sort by pair, a
+//      gather and a reduce-by-key with xs::CandMerge give one candidate per
+//      pair;
+//   row-wise (default): A's columns (csc_kernel) and rows
 //      (csr_kernel), then row_kernel, one block per read a, accumulates a's
 //      partners b > a in a shared-memory hash table (count + 64-bit minimum
 //      seed key per partner, shared-memory atomics): once to count, once to
@@ -481,7 +482,7 @@ int sort_product(Arena &ar, const Front &f, std::vector<Pair> &out_pairs,
 
 // *done = false when some read's table overflowed (nothing written).
 int row_product(Arena &ar, const Front &f, std::vector<Pair> &out_pairs,
-                std::vector<uint32_t> &out_shared, bool *done)
+                std::vector<uint32_t> &out_shared, bool *done, uint64_t *nonzeros)
 {
     *done = false;
     const int n_runs = f.n_runs, n_reads = (int)f.n_reads;
@@ -499,6 +500,7 @@ int row_product(Arena &ar, const Front &f, std::vector<Pair> &out_pairs,
     XS_CK(cub::DeviceScan::InclusiveSum(tmp, bytes, ucnt, col_end, n_runs, ar.s));
     uint32_t nnz = 0;
     if (int rc = read_back(ar, &nnz, col_end + (n_runs - 1))) return rc;
+    *nonzeros = nnz;
     if (nnz == 0) {
         *done = true;
         return XDROP_OK;
@@ -629,8 +631,8 @@ int find_candidates(cudaStream_t st, int sm_count, size_t budget, const uint32_t
         stats.runs = rc ? 0 : (uint64_t)std::max(f.n_runs, 0);
         bool done = rc != XDROP_OK || f.n_runs <= 0;
         const bool rows_ok = n_reads < kMaxItems;  // one block per read
-        if (!done && (flags & XDROP_SEEDS_ROWWISE) && rows_ok) {
-            rc = row_product(ar, f, out_pairs, out_shared, &done);
+        if (!done && !(flags & XDROP_SEEDS_SORT) && rows_ok) {
+            rc = row_product(ar, f, out_pairs, out_shared, &done, &stats.nonzeros);
             if (done && !rc) stats.product = XDROP_SEEDS_ROWWISE;
         }
         if (!done && !rc) rc = sort_product(ar, f, out_pairs, out_shared);

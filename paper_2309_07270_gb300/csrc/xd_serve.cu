@@ -206,6 +206,9 @@ cudaError_t Server::ensure_kernel()
     h_ctl_init->ring_alive = serve_ring_warps(grid);
     cudaError_t e = cudaMemcpyAsync(&d_ctl->ring_alive, &h_ctl_init->ring_alive, sizeof(unsigned int),
                                     cudaMemcpyHostToDevice, s_kernel);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&d_ctl->idle_ns, &h_ctl_init->idle_ns, sizeof(unsigned long long),
+                            cudaMemcpyHostToDevice, s_kernel);
     if (e == cudaSuccess) e = set_flag(this, &d_ctl->stop, 0, s_kernel);
     if (e == cudaSuccess) e = set_flag(this, &d_ctl->abort, 0, s_kernel);
     stop_sent = false;
@@ -491,7 +494,7 @@ void Server::run()
 Server *server_create(int device, int sm_count, size_t device_budget, Tile tile,
                       const ResidentReads &rr, const uint32_t *read_len_host,
                       int32_t *wide_scratch, int64_t wide_per_cta, int wide_grid,
-                      std::string &err)
+                      uint64_t idle_ns, std::string &err)
 {
     cudaSetDevice(device);
     Server *s = new Server();
@@ -540,7 +543,7 @@ Server *server_create(int device, int sm_count, size_t device_budget, Tile tile,
         s->h_flags[0] = 0;
         s->h_flags[1] = 1;
         memset(s->h_ctl_init, 0, sizeof(ServeCtl));
-        s->h_ctl_init->idle_ns = kIdleNs;
+        s->h_ctl_init->idle_ns = idle_ns ? idle_ns : kIdleNs;
         e = cudaMemcpy(s->d_ctl, s->h_ctl_init, sizeof(ServeCtl), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
@@ -645,8 +648,15 @@ ServerStats server_stats(Server *s)
         st.spill_reserved = c.spill_tail;
         st.spill_taken = c.spill_head;
         st.ring_warps = c.ring_alive;
+        st.idle_exits = c.idle_exits;
     }
     return st;
+}
+
+void server_set_idle_ns(Server *s, uint64_t idle_ns)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->h_ctl_init->idle_ns = idle_ns ? idle_ns : kIdleNs;
 }
 
 void server_destroy(Server *s)

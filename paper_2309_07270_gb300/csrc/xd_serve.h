@@ -28,6 +28,7 @@ struct ServerStats {
     uint64_t max_in_flight = 0; // admitted requests at once
     uint64_t admission_waits = 0;
     uint64_t published = 0, consumed = 0, spill_reserved = 0, spill_taken = 0, ring_warps = 0;
+    uint64_t idle_exits = 0;    // first-tier warps that left on the idle bound (all launches)
 };
 
 class Server;
@@ -38,7 +39,7 @@ class Server;
 Server *server_create(int device, int sm_count, size_t device_budget, Tile tile,
                       const ResidentReads &rr, const uint32_t *read_len_host,
                       int32_t *wide_scratch, int64_t wide_per_cta, int wide_grid,
-                      std::string &err);
+                      uint64_t idle_ns, std::string &err);
 // Copies the pairs; returns 0 or an XDROP_* error.
 int server_submit(Server *s, const xdrop_pair *pairs, size_t n_pairs, const Scoring &sc,
                   xdrop_result *out, uint64_t *ticket, std::string &err);
@@ -46,6 +47,9 @@ int server_submit(Server *s, const xdrop_pair *pairs, size_t n_pairs, const Scor
 int server_sync(Server *s, uint64_t ticket, int64_t timeout_ns, std::string &err);
 bool server_owns(Server *s, uint64_t ticket);
 ServerStats server_stats(Server *s);
+// Bound of a serving group's wait for work (hang guard), from the next
+// kernel launch on; 0 restores the default.
+void server_set_idle_ns(Server *s, uint64_t idle_ns);
 void server_destroy(Server *s);
 
 // Serving kernel launchers (tile families; the second tier follows from

@@ -42,17 +42,6 @@ int occupancy_mid(Tile t)
     return -1;
 }
 
-cudaError_t launch_window_plain(const Job *jp, uint32_t task_base, uint32_t n_tasks, Spill sp,
-                                cudaStream_t s)
-{
-    const uint64_t threads = (uint64_t)n_tasks * 32;
-    const unsigned grid = (unsigned)((threads + 255) / 256);
-    if (grid == 0) return cudaSuccess;
-    (void)cudaGetLastError();
-    window_kernel<32, 4, false><<<grid, 256, 0, s>>>(jp, task_base, n_tasks, sp);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_spill_mid(int grid, const Job *jp, Spill in, Spill out, cudaStream_t s)
 {
     (void)cudaGetLastError();

@@ -60,6 +60,35 @@ cudaError_t launch_binning(const Job *jp, uint64_t n_pairs, int grid, uint32_t *
     return cudaGetLastError();
 }
 
+cudaError_t launch_length_hist(const Job *jp, int grid, uint32_t *hist, cudaStream_t s)
+{
+    (void)cudaGetLastError();
+    bin_count_kernel<<<grid, BIN_THREADS, 0, s>>>(jp, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_pairs(const Pair *src, uint64_t n, uint32_t stride, uint32_t seed,
+                                Pair *dst, uint64_t m, cudaStream_t s)
+{
+    if (!m) return cudaSuccess;
+    (void)cudaGetLastError();
+    const uint64_t blocks = (m + 255) / 256;
+    sample_pairs_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, n, stride,
+                                                                                seed, dst, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_setup(uint64_t n_pairs, uint64_t sub_pairs, uint32_t *order, uint32_t *ctl,
+                              cudaStream_t s)
+{
+    if (!n_pairs) return cudaSuccess;
+    (void)cudaGetLastError();
+    const uint64_t blocks = (2 * n_pairs + 255) / 256;
+    plain_setup_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(n_pairs, sub_pairs,
+                                                                               order, ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_revcomp(const uint32_t *pk, int64_t n_words, const uint64_t *read_off,
                            const uint32_t *read_len, uint32_t n_reads, uint32_t *out,
                            cudaStream_t s)
@@ -106,7 +135,6 @@ int occupancy_packed(Tile);
 cudaError_t launch_serve_packed(Tile, int, const ServeArgs &, const uint32_t *, int64_t,
                                 cudaStream_t, bool *);
 int serve_occupancy_packed(Tile);
-cudaError_t launch_window_plain(const Job *, uint32_t, uint32_t, Spill, cudaStream_t);
 cudaError_t launch_spill_mid(int, const Job *, Spill, Spill, cudaStream_t);
 
 cudaError_t launch_serve_narrow(Tile, int, const ServeArgs &, const uint32_t *, int64_t,
@@ -143,15 +171,15 @@ const Tile kTiles[N_TILES] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4
 
 bool tile_supported(Tile t, bool persistent)
 {
-    if (!persistent) return !t.packed && t.lanes == 32 && (t.c == 4 || t.c == 16);
+    if (!persistent) return !t.packed && t.lanes == 32 && t.c == 16;
     return persistent_blocks_per_sm(t) >= 0;
 }
 
 cudaError_t launch_window(Tile t, bool count, const Job *jp, uint32_t task_base,
                           uint32_t n_tasks, Spill spill, cudaStream_t s)
 {
+    (void)t;
     if (count) return launch_window_count(jp, task_base, n_tasks, spill, s);
-    if (t.lanes == 32 && t.c == 4) return launch_window_plain(jp, task_base, n_tasks, spill, s);
     return cudaErrorInvalidValue;
 }
 

@@ -56,6 +56,7 @@ struct ServeCtl {
     unsigned int yield;             // host: take no more tasks, leave when drained
     unsigned int ring_alive;        // first-tier warps still running (host sets)
     unsigned int abort;             // host: leave now, abandoning tasks (teardown)
+    unsigned int idle_exits;        // first-tier warps that left on the idle bound
     alignas(128) unsigned long long consumed;    // ring entries taken (device CAS)
     alignas(128) unsigned long long spill_tail;  // second-tier queue: entries reserved
     alignas(128) unsigned long long spill_head;  // second-tier queue: entries taken

@@ -24,8 +24,8 @@ XDROP_EBUSY = -5
 XDROP_MODE_BATCHED = 0
 XDROP_MODE_PLAIN = 1
 XDROP_MODE_SERVE = 2
-XDROP_SEEDS_SORT = 0
-XDROP_SEEDS_ROWWISE = 1
+XDROP_SEEDS_ROWWISE = 0
+XDROP_SEEDS_SORT = 1
 XDROP_STATUS_OK = 0
 XDROP_STATUS_INVALID = 1
 XDROP_STATUS_TOO_LONG = 2
@@ -44,7 +44,8 @@ EXPORTS = ["xdrop_init", "xdrop_submit", "xdrop_submit_device", "xdrop_sync",
            "xdrop_count_cells_device", "xdrop_last_spills", "xdrop_set_tile",
            "xdrop_align_static", "xdrop_static_last_error", "xdrop_load_reads",
            "xdrop_submit_pairs", "xdrop_get_serve_stats", "xdrop_best_seeds_device",
-           "xdrop_find_candidates", "xdrop_get_seed_stats", "xdrop_accept_device"]
+           "xdrop_find_candidates", "xdrop_get_seed_stats", "xdrop_accept_device",
+           "xdrop_set_serve_idle"]
 
 
 class XdropError(RuntimeError):
@@ -72,7 +73,8 @@ class ServeStats(ctypes.Structure):
                 ("relaunches", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint64),
                 ("admission_waits", ctypes.c_uint64), ("published", ctypes.c_uint64),
                 ("consumed", ctypes.c_uint64), ("spill_reserved", ctypes.c_uint64),
-                ("spill_taken", ctypes.c_uint64), ("ring_warps", ctypes.c_uint64)]
+                ("spill_taken", ctypes.c_uint64), ("ring_warps", ctypes.c_uint64),
+                ("idle_exits", ctypes.c_uint64)]
 
 
 class KmerParams(ctypes.Structure):
@@ -88,7 +90,8 @@ class AcceptParams(ctypes.Structure):
 class SeedStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("occurrences", ctypes.c_uint64),
                 ("runs", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
-                ("product", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("product", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("nonzeros", ctypes.c_uint64)]
 
 
 _lib = None
@@ -126,13 +129,14 @@ def load():
     lib.xdrop_submit_pairs.argtypes = [vp, vp, sz, ctypes.POINTER(Scoring), vp,
                                        ctypes.POINTER(u64)]
     lib.xdrop_get_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    lib.xdrop_set_serve_idle.argtypes = [vp, u64]
     lib.xdrop_find_candidates.argtypes = [vp, ctypes.POINTER(KmerParams), vp, vp, sz,
                                           ctypes.POINTER(sz)]
     lib.xdrop_get_seed_stats.argtypes = [vp, ctypes.POINTER(SeedStats)]
     lib.xdrop_accept_device.argtypes = [vp, vp, vp, sz, vp, u32, ctypes.POINTER(AcceptParams), vp]
     for name in ("xdrop_load_reads", "xdrop_submit_pairs", "xdrop_get_serve_stats",
                  "xdrop_best_seeds_device", "xdrop_find_candidates", "xdrop_get_seed_stats",
-                 "xdrop_accept_device"):
+                 "xdrop_accept_device", "xdrop_set_serve_idle"):
         getattr(lib, name).restype = ctypes.c_int
     lib.xdrop_align_static.argtypes = [vp, u64, vp, vp, u32, vp, sz, ctypes.POINTER(Scoring),
                                        u32, vp, vp]
@@ -271,6 +275,11 @@ def xdrop_get_serve_stats(ctx) -> dict:
     return {k: getattr(st, k) for k, _ in ServeStats._fields_}
 
 
+def xdrop_set_serve_idle(ctx, idle_ns):
+    """Serving hang guard: bound (ns) of a group's wait for work."""
+    _check(load().xdrop_set_serve_idle(ctx, ctypes.c_uint64(int(idle_ns))), ctx)
+
+
 def xdrop_set_tile(ctx, lanes, cells):
     _check(load().xdrop_set_tile(ctx, int(lanes), int(cells)), ctx)
 
@@ -280,10 +289,11 @@ def xdrop_best_seeds_device(ctx, pairs_ptr, results_ptr, n, match, best_ptr):
                                           best_ptr), ctx)
 
 
-def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1, rowwise=False):
+def xdrop_find_candidates(ctx, k=31, lo=20, hi=30, stride=1, rowwise=True):
     """Candidate pairs of the resident reads (pairs as PAIR_DTYPE, ready for
     xdrop_submit_pairs) and their shared reliable k-mer counts; ``rowwise``
-    selects the row-wise product (same result)."""
+    (the default) runs the row-wise product, False the sort-based one (same
+    result)."""
     prm = KmerParams(int(k), int(stride), int(lo), int(hi),
                      XDROP_SEEDS_ROWWISE if rowwise else XDROP_SEEDS_SORT)
     n = ctypes.c_size_t()
@@ -368,7 +378,7 @@ class Aligner:
         return best[: dev.n_pairs]
 
     def find_candidates(self, packed, read_off, read_len, k=31, lo=20, hi=30, stride=1,
-                        rowwise=False):
+                        rowwise=True):
         """Load a read set and return its candidate pairs and shared counts
         (xdrop_find_candidates); the reads stay resident for submit_pairs."""
         xdrop_load_reads(self.ctx, packed, read_off, read_len)

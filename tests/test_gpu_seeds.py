@@ -1,16 +1,10 @@
 """Seed discovery on the GPU (xdrop_find_candidates: reliable k-mers and
 candidate read pairs) against the oracle (oracle/seeds.py), record for
-record (the default, sort-based product; the row-wise one is tested in
-test_gpu_seeds_rowwise.py), and its candidates aligned through
-xdrop_submit_pairs against the oracle's alignments.  At the paper's parameters (k = 31, frequency window
-[20, 50], 29x coverage) the output is checked by properties that hold at
-any size and against the CPU emulation of the same pipeline.  Collected
-after the other GPU files, so that a run stopping at the first failure has
-already run them."""
+record: the sort-based product here, the row-wise one (the default) in
+test_gpu_seeds_rowwise.py, both at the paper's parameters (k = 31, stride
+1, frequency window [20, 50], 29x coverage); and the candidates aligned
+through xdrop_submit_pairs against the oracle's alignments."""
 import ctypes
-import os
-import shutil
-import subprocess
 
 import numpy as np
 import pytest
@@ -19,7 +13,6 @@ from oracle import seeds as S
 from paper_2309_07270_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
@@ -136,7 +129,9 @@ def test_result_cache_and_errors(X):
         same(as_candidates(*X.xdrop_find_candidates(al.ctx, 13, 1, 1024)), want13)
         same(as_candidates(*X.xdrop_find_candidates(al.ctx, 9, 2, 6)), want9)   # new params
         same(as_candidates(*X.xdrop_find_candidates(al.ctx, 13, 1, 1024)), want13)
-        assert X.xdrop_get_seed_stats(al.ctx)["product"] == X.XDROP_SEEDS_SORT
+        st = X.xdrop_get_seed_stats(al.ctx)
+        assert st["product"] == X.XDROP_SEEDS_ROWWISE  # the default
+        assert st["nonzeros"] > 0
         # a short output buffer gets the first records and the total
         prm = X.KmerParams(13, 1, 1, 1024, 0)
         buf = np.zeros(3, X.PAIR_DTYPE)
@@ -166,53 +161,36 @@ def test_result_cache_and_errors(X):
 
 
 @pytest.fixture(scope="module")
-def emu(tmp_path_factory):
-    gxx = shutil.which("g++")
-    if gxx is None:
-        pytest.skip("no g++")
-    so = tmp_path_factory.mktemp("seeds_emu") / "libseeds_emu.so"
-    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-o", str(so),
-                    os.path.join(HERE, "seeds_emulator.cpp")], check=True)
-    lib = ctypes.CDLL(str(so))
-    vp, u32 = ctypes.c_void_p, ctypes.c_uint32
-    lib.emulate_candidates.restype = ctypes.c_int64
-    lib.emulate_candidates.argtypes = [vp, vp, vp, u32, u32, u32, u32, u32, vp, ctypes.c_int64]
-
-    def run(packed, off, lens, k, lo, hi, stride=1):
-        args = [packed.ctypes.data, off.ctypes.data, lens.ctypes.data, len(lens), k, stride, lo, hi]
-        n = lib.emulate_candidates(*args, None, 0)
-        out = np.zeros(6 * max(n, 1), np.uint32)
-        lib.emulate_candidates(*args, out.ctypes.data, n)
-        return out[:6 * n].view(S.CANDIDATE)
-
-    return run
-
-
-def test_paper_parameters_29x(X, emu):
+def paper29():
     """k = 31, window [20, 50], 29x coverage of a 100 kb genome with
     accurate reads (1% errors; at 12% almost no 31-mer reaches a count of
-    20): about 3 Mb in 290 reads.  Every candidate is a pair a < b in
-    order, its seed is an exact k-mer match on the named strand (sampled),
-    and the whole output equals the CPU emulation of the pipeline; both
-    products agree."""
+    20): about 3 Mb in 290 reads, and the oracle's candidates (about a
+    minute on one core)."""
     packed, off, lens = W.sequencing_reads(100_000, 29, 10_000, 6_000, 1_000, seed=29,
                                            error_rate=0.01)
     packed = np.ascontiguousarray(packed, np.uint32)
     off = np.ascontiguousarray(off, np.uint64)
     lens = np.ascontiguousarray(lens, np.uint32)
-    got = gpu(X, packed, off, lens, 31, 20, 50)
-    assert len(got) > 1000 and (got["b"] >> 31).sum() > 100
+    return packed, off, lens, S.candidate_pairs(packed, off, lens, k=31, lo=20, hi=50)
+
+
+@pytest.mark.parametrize("rowwise", [False, True], ids=["sort", "rowwise"])
+def test_paper_parameters_29x(X, paper29, rowwise):
+    """The paper's seed parameters: both products equal the oracle record
+    for record; every candidate is a pair a < b in (a, b) order and its
+    seed is an exact k-mer match on the strand it names."""
+    packed, off, lens, want = paper29
+    assert len(want) > 1000 and (want["b"] >> 31).sum() > 100
+    got = gpu(X, packed, off, lens, 31, 20, 50, rowwise=rowwise)
+    same(got, want)
     key = got["a"].astype(np.int64) * len(lens) + (got["b"] & 0x7FFFFFFF)
     assert np.all(np.diff(key) > 0) and np.all(got["a"] < (got["b"] & 0x7FFFFFFF))
     assert np.all(got["seed_len"] == 31) and np.all(got["shared"] >= 1)
     w = W.Workload("reads", packed, off, lens, np.zeros(0, W.PAIR_DTYPE))
-    rng = np.random.default_rng(0)
-    for i in rng.choice(len(got), size=min(2000, len(got)), replace=False):
-        c = got[i]
+    for c in got:
         a = w.codes(int(c["a"]))
         b = w.codes(int(c["b"]) & 0x7FFFFFFF)
         if c["b"] >> 31:
             b = W.revcomp(b)
         sa, sb = int(c["seed_a"]), int(c["seed_b"])
         assert np.array_equal(a[sa:sa + 31], b[sb:sb + 31])
-    same(got, emu(packed, off, lens, 31, 20, 50))

@@ -1,7 +1,7 @@
-"""The row-wise product of seed discovery (XDROP_SEEDS_ROWWISE) on the GPU
-against the oracle and against the sort-based product, including the
-fallback when a read's shared-memory table overflows.  Collected after
-every other GPU file: this product has the least GPU history."""
+"""The row-wise product of seed discovery (XDROP_SEEDS_ROWWISE, the default)
+on the GPU against the oracle, including the fallback to the sort-based
+product when a read's shared-memory table overflows.  The paper's
+parameters are tested for both products in test_gpu_seeds.py."""
 import numpy as np
 import pytest
 
@@ -71,12 +71,3 @@ def test_rowwise_table_overflow_falls_back(X):
         want = S.candidate_pairs(packed, off, lens, k=8, lo=1, hi=1024)
         assert (want["a"] == 0).sum() == n_leaves
         same(gpu(X, packed, off, lens, 8, 1, 1024, rowwise=True, expect_product=product), want)
-
-
-def test_rowwise_paper_parameters_29x(X):
-    """Both products agree on the paper's parameters at 29x."""
-    packed, off, lens = W.sequencing_reads(100_000, 29, 10_000, 6_000, 1_000, seed=29,
-                                           error_rate=0.01)
-    want = gpu(X, packed, off, lens, 31, 20, 50)
-    assert len(want) > 1000
-    same(gpu(X, packed, off, lens, 31, 20, 50, rowwise=True), want)

@@ -237,3 +237,34 @@ def test_reverse_strand_requests(X, orc):
         want = orc.align_pairs(w.packed, w.read_off, w.read_len, w.pairs[idx], 1, -1, -1, 50,
                                nthreads=8)
         assert np.array_equal(outs[k].view(np.int32), want.view(np.int32))
+
+
+def test_idle_bound_ends_the_kernel_and_the_context_recovers(X, orc, pool):
+    """The hang guard, without a fault: with a 2 ms idle bound the serving
+    kernel's first-tier warps stop waiting for work on their own (counted in
+    idle_exits, the status the host reads) well before the host's own idle
+    stop, the kernel ends, and the next request launches it again and is
+    exact."""
+    sc = X.scoring(1, -1, -1, 50)
+    ctx = X.xdrop_init(0, 0, X.XDROP_MODE_SERVE)
+    try:
+        X.xdrop_set_serve_idle(ctx, 2_000_000)
+        X.xdrop_load_reads(ctx, pool.packed, pool.read_off, pool.read_len)
+        first = run_alone(X, ctx, pool, [(0, np.arange(0, 300))], sc)[0]
+        deadline = time.monotonic() + 5.0
+        st = X.xdrop_get_serve_stats(ctx)
+        while time.monotonic() < deadline and not (st["idle_exits"] > 0 and st["ring_warps"] == 0):
+            time.sleep(0.002)
+            st = X.xdrop_get_serve_stats(ctx)
+        assert st["idle_exits"] > 0 and st["ring_warps"] == 0, st
+        launches = st["relaunches"]
+        second = run_alone(X, ctx, pool, [(0, np.arange(300, 600))], sc)[0]
+        st2 = X.xdrop_get_serve_stats(ctx)
+    finally:
+        X.xdrop_free(ctx)
+    assert st2["relaunches"] > launches
+    assert st2["requests_done"] == 2
+    for out, idx in ((first, np.arange(0, 300)), (second, np.arange(300, 600))):
+        want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
+                               1, -1, -1, 50, nthreads=8)
+        assert np.array_equal(out.view(np.int32), want.view(np.int32))
