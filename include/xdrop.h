@@ -172,7 +172,8 @@ int xdrop_submit(xdrop_ctx *c, const uint32_t *packed, const uint64_t *read_off,
  * needs the reverse complements only the host-side calls store) gets
  * status XDROP_STATUS_INVALID and zero scores, the others are aligned,
  * and the ticket's sync returns XDROP_EINVAL.  Results are written to
- * `out` (device) by the time sync returns. */
+ * `out` (device) by the time sync returns; until then `out` may also hold
+ * the library's scratch (autotuning samples its pairs there). */
 int xdrop_submit_device(xdrop_ctx *c, const uint32_t *packed, uint64_t n_words,
                         const uint64_t *read_off, const uint32_t *read_len,
                         uint32_t n_reads, const xdrop_pair *pairs,

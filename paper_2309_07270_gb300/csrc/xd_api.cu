@@ -128,7 +128,6 @@ struct xdrop_ctx {
     Tile forced = {0, 0};         // xdrop_set_tile
     // tuned first tile per (scoring, length bucket of the job)
     std::map<std::tuple<int, int, int, int, int>, Tile> tuned;
-    DevBuf tune_pairs, tune_out;  // autotuning sample and its results
     uint64_t scratch_version = 0; // bumped whenever a scratch buffer moves
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev_main0 = nullptr, ev_main1 = nullptr;  // recorded inside the graph
@@ -283,19 +282,23 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     // 32-bit tiles on an eighth.  The sample is stratified and random (one
     // pair out of every block of 3 or 8, seeded), so it has the job's
     // length mix even when the input is sorted or clustered.
+    //
+    // The sample and its results live in the job's own result buffer
+    // (48 bytes per sampled pair, at most 16 of the 28 bytes per pair there),
+    // so tuning needs no memory beyond the submit's; the buffer is zeroed
+    // afterwards, before validation writes the status words.
     const bool packed = packed_scoring_ok(job.sc);
     const uint32_t stride = job.n_pairs <= 3 * 4096 ? 1u : (packed ? 3u : 8u);
     const uint64_t m = (job.n_pairs + stride - 1) / stride;
-    int rc0;
-    if ((rc0 = dev_alloc(c, c->tune_pairs, std::max<uint64_t>(m, 1) * sizeof(Pair)))) return rc0;
-    if ((rc0 = dev_alloc(c, c->tune_out, std::max<uint64_t>(m, 1) * sizeof(xdrop_result))))
-        return rc0;
-    CK(launch_sample_pairs(job.pairs, job.n_pairs, stride, 0x5eed1234u, (Pair *)c->tune_pairs.p, m,
-                           s));
     Job js = job;
-    js.pairs = (const Pair *)c->tune_pairs.p;
-    js.out = (int32_t *)c->tune_out.p;
-    js.n_pairs = m;
+    if (stride > 1) {
+        Pair *sp = (Pair *)job.out;
+        int32_t *so = job.out + m * (sizeof(Pair) / 4);
+        CK(launch_sample_pairs(job.pairs, job.n_pairs, stride, 0x5eed1234u, sp, m, s));
+        js.pairs = sp;
+        js.out = so;
+        js.n_pairs = m;
+    }
     CK(cudaStreamSynchronize(s));
     *tk->h_job = js;
     CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
@@ -325,9 +328,10 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // restore the full job for the real run
+    // restore the full job for the real run, with a clean result buffer
     *tk->h_job = job;
     CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(job.out, 0, job.n_pairs * sizeof(xdrop_result), s));
     CK(cudaStreamSynchronize(s));
     return best->lanes ? XDROP_OK : fail(XDROP_ECUDA, "no tile could be timed");
 }
@@ -479,13 +483,15 @@ int launch_ticket(xdrop_ctx *c, Ticket *tk, const Job &job, uint32_t maxlen)
     *tk->h_job = job;
     CK(cudaMemcpyAsync(c->d_job, tk->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(tk->ev_begin, s));
+    // the tile first: autotuning uses the result buffer as scratch, and
+    // validation then writes every status word
+    if (job.n_pairs && c->mode != XDROP_MODE_PLAIN) {
+        if ((rc = pick_tile(c, tk, job, &c->tile0))) return rc;
+    }
     if (tk->device_submit) {
         CK(cudaMemsetAsync(c->d_ctrs + C_NBAD, 0, 4, s));
         CK(launch_validate(c->d_job, job.n_pairs, c->d_ctrs + C_NBAD, s));
         tk->launches += 1;
-    }
-    if (job.n_pairs && c->mode != XDROP_MODE_PLAIN) {
-        if ((rc = pick_tile(c, tk, job, &c->tile0))) return rc;
     }
     if (job.n_pairs) {
         if (c->mode == XDROP_MODE_PLAIN) rc = run_plain(c, tk, job);
@@ -822,8 +828,6 @@ void xdrop_free(xdrop_ctx *c)
     if (c->ev_main1) cudaEventDestroy(c->ev_main1);
     cudaFree(c->order.p);
     cudaFree(c->plain_ctl.p);
-    cudaFree(c->tune_pairs.p);
-    cudaFree(c->tune_out.p);
     for (auto &s : c->spill) cudaFree(s.p);
     cudaFree(c->wide.p);
     cudaFree(c->d_job);

@@ -635,7 +635,10 @@ int find_candidates(cudaStream_t st, int sm_count, size_t budget, const uint32_t
             rc = row_product(ar, f, out_pairs, out_shared, &done, &stats.nonzeros);
             if (done && !rc) stats.product = XDROP_SEEDS_ROWWISE;
         }
-        if (!done && !rc) rc = sort_product(ar, f, out_pairs, out_shared);
+        if (!done && !rc) {
+            rc = sort_product(ar, f, out_pairs, out_shared);
+            if (!rc) stats.product = XDROP_SEEDS_SORT;
+        }
         if (!rc) rc = ar.cuda(cudaEventRecord(ev[1], st), "cudaEventRecord");
         if (!rc) rc = ar.cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
         if (!rc) {
