@@ -17,8 +17,9 @@
 //   row-wise (default): A's columns (csc_kernel) and rows
 //      (csr_kernel), then row_kernel, one block per read a, accumulates a's
 //      partners b > a in a shared-memory hash table (count + 64-bit minimum
-//      seed key per partner, shared-memory atomics): once to count, once to
-//      write; a radix sort of the few candidates orders them.  No per-entry
+//      seed key per partner, shared-memory atomics) in one pass, staging up
+//      to 256 partners per read (a second pass rewrites the rare reads with
+//      more); a radix sort of the few candidates orders them.  No per-entry
 //      table exists.  A read with more partners than the table holds makes
 //      the call take the sort-based product instead (same result).
 // The sorts, run-length encoding, scans and reduce-by-key are CUB library
@@ -178,16 +179,31 @@ csr_kernel(const uint64_t *__restrict__ members, const uint32_t *__restrict__ co
 }
 
 // One block per read a: the partners b > a of a in a shared-memory table.
-// WRITE = false: cand_cnt[a] = number of partners (0 and the overflow flag
-// when the table is full).  WRITE = true: the partners' records at
-// cand_end[a-1] ..., in table order.
+// Partners of a read kept in its staging area by the first pass; a read
+// with more goes through the second pass.
+constexpr uint32_t kStage = 256;
+
+// Per-read staging of the first pass: partner id, 64-bit best seed and
+// shared count of up to kStage partners of every read.
+struct Stage {
+    uint32_t *key;
+    unsigned long long *best;
+    uint32_t *cnt;
+};
+
+// WRITE = false (first pass, block a = read a): cand_cnt[a] = number of
+// partners (0 and the overflow flag when the table is full); up to kStage
+// partners go to a's staging area, a read with more is listed in big.
+// WRITE = true (second pass, block i = read big[i]): the partners' records
+// at cand_end[a-1] ..., in table order.
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 row_kernel(const uint32_t *__restrict__ row_end, const uint32_t *__restrict__ row_col,
            const uint32_t *__restrict__ row_pos, const uint32_t *__restrict__ col_end,
            const uint64_t *__restrict__ members, const uint32_t *__restrict__ read_len,
            uint32_t k, uint32_t nb, uint64_t *__restrict__ cand_cnt,
-           const uint64_t *__restrict__ cand_end, uint32_t *__restrict__ overflow,
+           const uint64_t *__restrict__ cand_end, uint32_t *__restrict__ overflow, Stage stage,
+           uint32_t *__restrict__ big, uint32_t *__restrict__ n_big,
            uint64_t *__restrict__ rkey, unsigned long long *__restrict__ rbest,
            uint32_t *__restrict__ rshared, uint32_t *__restrict__ ridx)
 {
@@ -195,7 +211,7 @@ row_kernel(const uint32_t *__restrict__ row_end, const uint32_t *__restrict__ ro
     __shared__ uint32_t tkey[kSlots], tcnt[kSlots];
     __shared__ unsigned long long tbest[kSlots];
     __shared__ uint32_t ovf, cursor;
-    const uint32_t a = blockIdx.x;
+    const uint32_t a = WRITE ? big[blockIdx.x] : blockIdx.x;
     const uint32_t e0 = a ? row_end[a - 1] : 0, e1 = row_end[a];
     if (e0 == e1) {  // a holds no reliable k-mer
         if (!WRITE && threadIdx.x == 0) cand_cnt[a] = 0;
@@ -235,7 +251,23 @@ row_kernel(const uint32_t *__restrict__ row_end, const uint32_t *__restrict__ ro
         n = __reduce_add_sync(0xFFFFFFFFu, n);
         if (lane == 0) atomicAdd(&cursor, n);
         __syncthreads();
-        if (threadIdx.x == 0) cand_cnt[a] = cursor;
+        const uint32_t total = cursor;
+        if (threadIdx.x == 0) {
+            cand_cnt[a] = total;
+            if (total > kStage) big[atomicAdd(n_big, 1u)] = a;
+        }
+        if (total > kStage) return;  // the second pass writes this read
+        __syncthreads();
+        if (threadIdx.x == 0) cursor = 0;
+        __syncthreads();
+        const uint64_t base = (uint64_t)a * kStage;
+        for (uint32_t h = threadIdx.x; h < kSlots; h += blockDim.x) {
+            if (tkey[h] == xs::kEmpty) continue;
+            const uint64_t i = base + atomicAdd(&cursor, 1u);
+            stage.key[i] = tkey[h];
+            stage.best[i] = tbest[h];
+            stage.cnt[i] = tcnt[h];
+        }
     } else {
         const uint64_t base = a ? cand_end[a - 1] : 0;
         for (uint32_t h = threadIdx.x; h < kSlots; h += blockDim.x) {
@@ -244,6 +276,31 @@ row_kernel(const uint32_t *__restrict__ row_end, const uint32_t *__restrict__ ro
             rkey[i] = ((uint64_t)a << nb) | tkey[h];
             rbest[i] = tbest[h];
             rshared[i] = tcnt[h];
+            ridx[i] = (uint32_t)i;
+        }
+    }
+}
+
+// The staged partners of every read with at most kStage of them, to their
+// records at cand_end[a-1] ...; a warp per read.
+__global__ void __launch_bounds__(kThreads)
+stage_out_kernel(const uint64_t *__restrict__ cand_cnt, const uint64_t *__restrict__ cand_end,
+                 Stage stage, uint32_t n_reads, uint32_t nb, uint64_t *__restrict__ rkey,
+                 unsigned long long *__restrict__ rbest, uint32_t *__restrict__ rshared,
+                 uint32_t *__restrict__ ridx)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_reads;
+         a += warps) {
+        const uint64_t n = cand_cnt[a];
+        if (n == 0 || n > kStage) continue;
+        const uint64_t base = a ? cand_end[a - 1] : 0;
+        for (uint32_t j = lane; j < n; j += 32) {
+            const uint64_t s = a * kStage + j, i = base + j;
+            rkey[i] = (a << nb) | stage.key[s];
+            rbest[i] = stage.best[s];
+            rshared[i] = stage.cnt[s];
             ridx[i] = (uint32_t)i;
         }
     }
@@ -527,25 +584,33 @@ int row_product(Arena &ar, const Front &f, std::vector<Pair> &out_pairs,
     csr_kernel<<<grid_for(nnz, f.sm_count), kThreads, 0, ar.s>>>(members, col_of, nnz, row_end,
                                                                  row_fill, row_col, row_pos);
     XS_CK(cudaGetLastError());
-    // each read's partners: count, then write
+    // each read's partners in one pass: counted, and staged when there are
+    // at most kStage of them; reads with more are recomputed and written
+    // by a second pass over those reads alone
     uint64_t *cand_cnt, *cand_end;
-    uint32_t *overflow;
+    uint32_t *flags, *big;  // flags[0]: table overflow, flags[1]: reads listed in big
+    Stage stage;
     XS_GET(cand_cnt, n_reads);
     XS_GET(cand_end, n_reads);
-    XS_GET(overflow, 1);
-    XS_CK(cudaMemsetAsync(overflow, 0, 4, ar.s));
-    row_kernel<false><<<n_reads, kThreads, 0, ar.s>>>(row_end, row_col, row_pos, col_end, members,
-                                                      f.read_len, f.k, f.nb, cand_cnt, nullptr,
-                                                      overflow, nullptr, nullptr, nullptr, nullptr);
+    XS_GET(flags, 2);
+    XS_GET(big, n_reads);
+    XS_GET(stage.key, (uint64_t)n_reads * kStage);
+    XS_GET(stage.best, (uint64_t)n_reads * kStage);
+    XS_GET(stage.cnt, (uint64_t)n_reads * kStage);
+    XS_CK(cudaMemsetAsync(flags, 0, 8, ar.s));
+    row_kernel<false><<<n_reads, kThreads, 0, ar.s>>>(
+        row_end, row_col, row_pos, col_end, members, f.read_len, f.k, f.nb, cand_cnt, nullptr,
+        flags, stage, big, flags + 1, nullptr, nullptr, nullptr, nullptr);
     XS_CK(cudaGetLastError());
     bytes = 0;
     XS_CK(cub::DeviceScan::InclusiveSum(nullptr, bytes, cand_cnt, cand_end, n_reads, ar.s));
     XS_GET(tmp, bytes);
     XS_CK(cub::DeviceScan::InclusiveSum(tmp, bytes, cand_cnt, cand_end, n_reads, ar.s));
-    uint32_t ovf = 0;
+    uint32_t hflags[2] = {0, 0};
     uint64_t n_cand = 0;
-    XS_CK(cudaMemcpyAsync(&ovf, overflow, 4, cudaMemcpyDeviceToHost, ar.s));
+    XS_CK(cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, ar.s));
     if (int rc = read_back(ar, &n_cand, cand_end + (n_reads - 1))) return rc;
+    const uint32_t ovf = hflags[0], n_big = hflags[1];
     if (ovf) return XDROP_OK;  // not done: the sort-based product takes over
     *done = true;
     if (n_cand == 0) return XDROP_OK;
@@ -562,10 +627,15 @@ int row_product(Arena &ar, const Front &f, std::vector<Pair> &out_pairs,
     XS_GET(ri1, n_cand);
     XS_GET(rbest, n_cand);
     XS_GET(rshared, n_cand);
-    row_kernel<true><<<n_reads, kThreads, 0, ar.s>>>(row_end, row_col, row_pos, col_end, members,
-                                                     f.read_len, f.k, f.nb, nullptr, cand_end,
-                                                     nullptr, rk0, rbest, rshared, ri0);
+    stage_out_kernel<<<grid_for((uint64_t)n_reads * 32, f.sm_count), kThreads, 0, ar.s>>>(
+        cand_cnt, cand_end, stage, (uint32_t)n_reads, f.nb, rk0, rbest, rshared, ri0);
     XS_CK(cudaGetLastError());
+    if (n_big) {
+        row_kernel<true><<<n_big, kThreads, 0, ar.s>>>(
+            row_end, row_col, row_pos, col_end, members, f.read_len, f.k, f.nb, nullptr, cand_end,
+            nullptr, stage, big, nullptr, rk0, rbest, rshared, ri0);
+        XS_CK(cudaGetLastError());
+    }
     // candidates in (a, b) order
     const int nc = (int)n_cand;
     cub::DoubleBuffer<uint64_t> rk(rk0, rk1);
