@@ -127,6 +127,23 @@ __device__ __forceinline__ unsigned group_mask(int gbase)
     else return ((1u << LANES) - 1u) << gbase;
 }
 
+// Maximum over the LANES lanes of each group, in code every lane of the
+// warp runs together (the lockstep loops): a butterfly of log2(LANES)
+// shuffle-and-max steps.  A redux with each group's own mask is serialised
+// over the warp's groups, about a quarter of the lockstep kernels' time
+// when measured; code whose groups diverge keeps the masked redux.
+template <int LANES>
+__device__ __forceinline__ int32_t lockstep_group_max(int32_t v)
+{
+    if constexpr (LANES == 32) {
+        return __reduce_max_sync(FULL, v);
+    } else {
+#pragma unroll
+        for (int off = 1; off < LANES; off <<= 1) v = max(v, __shfl_xor_sync(FULL, v, off, LANES));
+        return v;
+    }
+}
+
 template <int LANES, int C, bool COUNT>
 __device__ int extend_window(const Ext &e, const Scoring sc, int glane, int gbase,
                              int32_t &best, int32_t &best_i, int32_t &best_j,
@@ -627,7 +644,7 @@ __device__ __forceinline__ void lockstep_loop(Src &src, const uint32_t *pk, int6
     auto finish = [&](int32_t (&V)[C], int32_t lkey, const bool odd) {
         // The key orders cells within a lane only: take the lowest lane
         // whose maximum is M, then that lane's first cell holding it.
-        const int32_t mkey = __reduce_max_sync(gm, lkey);
+        const int32_t mkey = lockstep_group_max<L>(lkey);
         const int32_t M = mkey >> 4;
         const unsigned hits = __ballot_sync(FULL, (lkey >> 4) == M) & gm;
         const int src_lane = __ffs(hits) - 1;

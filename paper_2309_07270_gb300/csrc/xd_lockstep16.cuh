@@ -292,7 +292,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         }
         // Group key: value above lane above slot in lane, so one max finds
         // the lowest window slot among the cells holding the maximum.
-        const int32_t mkey = __reduce_max_sync(gm, (lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
+        const int32_t mkey = lockstep_group_max<L>((lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
         if (mkey >= xup) {  // best value - thr > x: T rises (decoded at retire)
             T += (mkey >> 9) - sc.x;
             bkey = mkey;
