@@ -135,10 +135,16 @@ typedef struct {
     uint64_t consumed;        /* extensions taken from it                    */
     uint64_t spill_reserved;  /* extensions handed to the second tier        */
     uint64_t spill_taken;     /* of those, taken by second-tier groups       */
-    uint64_t ring_warps;      /* first-tier warps of the running kernel      */
-    uint64_t idle_exits;      /* first-tier warps that left because no work
-                                 came within the idle bound (hang guard),
-                                 over all launches of the serving kernel    */
+    uint64_t ring_warps;      /* warps of the running serving kernel         */
+    uint64_t idle_exits;      /* warps that left because no work came within
+                                 the idle bound (hang guard), over all
+                                 launches of the serving kernel             */
+    uint64_t help_sessions;   /* times a warp left the first tier to serve
+                                 the second-tier queue (no warp is reserved
+                                 for it), over all launches                 */
+    uint64_t surplus_counts;  /* extensions counted past their request's
+                                 total: an invariant counter that stays 0
+                                 (each extension runs exactly once)         */
 } xdrop_serve_stats;
 
 /* Create a context on CUDA device `device`.  device_mem_budget bounds the

@@ -223,8 +223,12 @@ Spill spill_of(xdrop_ctx *c, int k)
 
 Tile next_tile_after(Tile t)
 {
-    // The 128-wide tile for narrower first tiers, then 512.
-    if (t.width() < 128) return Tile{16, 8};
+    // The 128-wide tile for narrower first tiers, then 512.  Its overflow
+    // tier is 32 lanes x 4 cells: the few extensions that reach it run one
+    // per warp, and with half the cells per lane a diagonal takes half as
+    // long, so the tier (which ends when its longest extension does) is
+    // shorter than with 16 lanes x 8 cells.
+    if (t.width() < 128) return Tile{32, 4};
     return Tile{32, 16};
 }
 
@@ -437,7 +441,7 @@ int run_plain(xdrop_ctx *c, Ticket *tk, const Job &job)
     if ((rc = dev_alloc(c, c->plain_ctl, n_sub * 8))) return rc;
     uint32_t *order = (uint32_t *)c->order.p, *ctl = (uint32_t *)c->plain_ctl.p;
     CK(launch_plain_setup(n_pairs, kSubBatchPairs, order, ctl, s));
-    const uint64_t groups_per_block = 256 / t0.lanes;
+    const uint64_t groups_per_block = (uint64_t)persistent_block_threads(t0) / t0.lanes;
     for (uint64_t k = 0; k < n_sub; ++k) {
         const uint64_t p0 = k * kSubBatchPairs, np = std::min(kSubBatchPairs, n_pairs - p0);
         const uint64_t blocks = (2 * np + groups_per_block - 1) / groups_per_block;
@@ -1063,6 +1067,8 @@ int xdrop_get_serve_stats(xdrop_ctx *c, xdrop_serve_stats *st)
         st->spill_taken = s.spill_taken;
         st->ring_warps = s.ring_warps;
         st->idle_exits = s.idle_exits;
+        st->help_sessions = s.help_sessions;
+        st->surplus_counts = s.surplus_counts;
     }
     return XDROP_OK;
 }

@@ -800,354 +800,6 @@ __device__ __forceinline__ void lockstep_loop(Src &src, const uint32_t *pk, int6
     }
 }
 
-// ---------------------------------------------------------------------------
-// Serving: a persistent kernel fed by a device ring of tasks that the host
-// keeps appending to while the kernel runs (continuous batching).  Ring
-// entry = slot << 24 | task; slot names the request's device Job.
-//
-// Most warps run the first-tier tile on ring tasks.  A task whose band
-// outgrows that tile goes to a device spill queue, which one warp in
-// sixteen serves with the next wider tile, so overflow never stops the
-// loop.  A task too wide for the second tier is listed in its request
-// (Job::spill_list, counted in ctr[1]) for the host's unbounded pass.
-// Every wait is bounded: ring warps leave after an idle limit (or on stop /
-// yield), spill warps once every ring warp has left and their queue is
-// empty; a queue entry that never appears sets the error word.
-// ---------------------------------------------------------------------------
-constexpr int kSpillWarpEvery = 16;
-constexpr uint32_t kSpillQueueMask = (1u << 16) - 1;
-constexpr int kEntrySpinLimit = 1 << 20;
-
-__device__ __forceinline__ unsigned long long globaltimer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-struct ServeArgs {
-    ServeCtl *ctl;
-    const uint32_t *ring;
-    uint32_t ring_mask;
-    uint32_t *spq;             // spill queue, entry + 1 (0 = empty)
-    const Job *slot_jobs;
-    uint32_t *done;            // mapped host: per slot tag and wide count; [2*64] error word
-    uint32_t n_slots;
-};
-
-// Count a finished task; the last one of a request publishes it.
-__device__ __forceinline__ void serve_count(const ServeArgs &a, const Job *gj, const Job &J)
-{
-    __threadfence();
-    const uint32_t f = atomicAdd(&J.ctr[0], 1u) + 1u;
-    if ((uint64_t)f == 2 * J.n_pairs) {
-        const size_t sl = (size_t)(gj - a.slot_jobs);
-        volatile uint32_t *d = a.done;
-        d[2 * sl + 1] = *(volatile const uint32_t *)&J.ctr[1];
-        __threadfence_system();
-        d[2 * sl] = J.tag;
-    }
-}
-
-// A task the second tier cannot hold: listed for the host's unbounded pass.
-__device__ __forceinline__ void serve_list_wide(const ServeArgs &a, const Job *gj, const Job &J,
-                                                uint32_t task)
-{
-    const uint32_t k = atomicAdd(&J.ctr[1], 1u);
-    J.spill_list[k] = task;
-    serve_count(a, gj, J);
-}
-
-constexpr unsigned long long kSpillBacklog = 64;  // ring warps switch tiers above this
-constexpr unsigned long long kDeepBacklog = 16384;  // ring positions: claim chunks above this
-constexpr unsigned long long kClaimChunk = 16;     // positions per claim with a deep backlog
-
-struct RingSrc {
-    static constexpr bool kCanAbort = true;  // teardown may stop the loop
-    ServeArgs a;
-    unsigned long long idle_since;
-    int backoff;   // loop turns before the next poll (leader)
-    int level;     // backoff doubling level (leader)
-    bool leaving;  // stop, yield or the idle bound (not a switch to the second tier)
-
-    unsigned long long buf_base = 0;  // claimed ring positions not yet handed out (leader)
-    int buf_n = 0;
-
-    // Warp-level fetch (see BatchSrc): one poll and one CAS for all the
-    // warp's waiting groups.  Every claimed position is below the published
-    // end, so it holds a task.  With a deep backlog the warp claims a chunk
-    // of kClaimChunk positions and hands the rest to its next waiting
-    // groups from its buffer, which cuts the number of CASes on `consumed`
-    // (under load most of them lose to another warp); a warp with a
-    // non-empty buffer neither switches tiers nor leaves.  A lost CAS race
-    // is retried at the next turn; only an empty ring starts the back-off.
-    __device__ __forceinline__ int fetch_warp(unsigned needm, int lane, int gbase, unsigned gm,
-                                              bool need, uint32_t &task, const Job *&gj)
-    {
-        int status = 0;  // 1 granted k entries, 0 none, -1 leave, -2 help the second tier
-        int k = 0;
-        unsigned long long base = 0;
-        if (lane == 0) {
-            const int want = __popc(needm);
-            if (buf_n > 0) {
-                k = buf_n < want ? buf_n : want;
-                base = buf_base;
-                buf_base += (unsigned long long)k;
-                buf_n -= k;
-                status = 1;
-            } else if (backoff > 0) {
-                --backoff;
-            } else {
-                volatile ServeCtl *v = a.ctl;
-                if (v->yield) {
-                    status = -1;
-                } else if (*(volatile unsigned long long *)&a.ctl->spill_tail -
-                               *(volatile unsigned long long *)&a.ctl->spill_head >
-                           kSpillBacklog) {
-                    status = -2;
-                } else {
-                    const unsigned long long pub = v->published;
-                    unsigned long long cons = *(volatile unsigned long long *)&a.ctl->consumed;
-                    for (int tries = 0; tries < 4 && cons < pub; ++tries) {
-                        const unsigned long long chunk =
-                            (pub - cons > kDeepBacklog) ? kClaimChunk : (unsigned long long)want;
-                        const unsigned long long kk = (pub - cons < chunk) ? pub - cons : chunk;
-                        const unsigned long long got = atomicCAS(&a.ctl->consumed, cons, cons + kk);
-                        if (got == cons) {
-                            base = cons;
-                            k = (kk < (unsigned long long)want) ? (int)kk : want;
-                            buf_base = cons + (unsigned long long)k;
-                            buf_n = (int)kk - k;
-                            status = 1;
-                            break;
-                        }
-                        cons = got;
-                    }
-                    if (status == 1) {
-                        idle_since = 0;
-                        level = 0;
-                    } else if (cons >= pub) {  // nothing published to take
-                        const unsigned long long now = globaltimer_ns();
-                        if (idle_since == 0) idle_since = now;
-                        if (v->stop) {
-                            status = -1;
-                        } else if (now - idle_since > v->idle_ns) {
-                            status = -1;  // hang guard: counted for the host
-                            atomicAdd(&a.ctl->idle_exits, 1u);
-                        }
-                        backoff = 1 << level;
-                        if (level < 6) ++level;
-                    }
-                }
-            }
-        }
-        // every lane takes part in the broadcasts before any lane returns
-        status = __shfl_sync(FULL, status, 0);
-        k = __shfl_sync(FULL, k, 0);
-        base = __shfl_sync(FULL, base, 0);
-        if (status == -1) leaving = true;
-        if (!need) return 0;
-        if (status < 0) return -1;
-        if (status == 0) return 0;
-        const int rank = __popc(needm & ((1u << gbase) - 1u));
-        if (rank >= k) return 0;
-        const uint32_t entry = *(volatile const uint32_t *)&a.ring[(base + rank) & a.ring_mask];
-        task = entry & 0xffffffu;
-        gj = &a.slot_jobs[entry >> 24];
-        return 1;
-    }
-    __device__ __forceinline__ void idle() { __nanosleep(2000); }
-    __device__ __forceinline__ bool aborted() const
-    {
-        return *(volatile const unsigned int *)&a.ctl->abort != 0u;
-    }
-    __device__ __forceinline__ Ext open(const Job *gj, uint32_t task, Scoring &sc)
-    {
-        const Job J = ldcg_job(gj);
-        sc = J.sc;
-        return decode_cg(J, task);
-    }
-    __device__ __forceinline__ void retire(const Job *gj, uint32_t task, bool overflow, int32_t T,
-                                           int32_t bi, int32_t bj)
-    {
-        const Job J = ldcg_job(gj);
-        if (!overflow) {
-            store_result_cg(J, task, T, bi, bj);
-            serve_count(a, gj, J);
-            return;
-        }
-        // Hand the task to the second tier (not counted yet).  Reserve a
-        // queue position only while the queue has room; the slot's previous
-        // occupant (one lap earlier) has been taken, and its taker clears
-        // the slot right after reading it.
-        volatile ServeCtl *v = a.ctl;
-        unsigned long long t = v->spill_tail;
-        for (int tries = 0; tries < 8; ++tries) {
-            if (t - v->spill_head > kSpillQueueMask) break;  // full
-            const unsigned long long got = atomicCAS(&a.ctl->spill_tail, t, t + 1);
-            if (got == t) {
-                volatile uint32_t *slot = (volatile uint32_t *)&a.spq[t & kSpillQueueMask];
-                bool free_slot = false;
-                for (int spin = 0; spin < kEntrySpinLimit; ++spin) {
-                    if (*slot == 0u) { free_slot = true; break; }
-                    __nanosleep(64);
-                }
-                if (!free_slot) {
-                    volatile uint32_t *d = a.done;
-                    d[2 * a.n_slots] = 1u;  // error word: the slot never drained
-                    __threadfence_system();
-                }
-                *slot = (((uint32_t)(gj - a.slot_jobs) << 24) | task) + 1u;
-                return;
-            }
-            t = got;
-        }
-        serve_list_wide(a, gj, J, task);  // queue full or contended: the host's pass
-    }
-};
-
-struct SpillSrc {
-    static constexpr bool kCanAbort = true;  // teardown may stop the loop
-    ServeArgs a;
-    int backoff;
-    int level;
-    bool dynamic;  // a ring warp helping out: leave as soon as the queue is empty
-    bool failed;
-
-    __device__ __forceinline__ int fetch_warp(unsigned needm, int lane, int gbase, unsigned gm,
-                                              bool need, uint32_t &task, const Job *&gj)
-    {
-        int status = 0;  // 1 granted k positions, 0 none, -1 leave
-        int k = 0;
-        unsigned long long base = 0;
-        if (lane == 0) {
-            if (backoff > 0) {
-                --backoff;
-            } else {
-                volatile ServeCtl *v = a.ctl;
-                // ring_alive before the queue ends: a ring warp pushes all
-                // its entries and fences before it counts itself out, so
-                // once none is left the tail read after the fence holds
-                // every entry there will ever be
-                const unsigned int alive = v->ring_alive;
-                __threadfence();
-                const unsigned long long tail = *(volatile unsigned long long *)&a.ctl->spill_tail;
-                unsigned long long head = *(volatile unsigned long long *)&a.ctl->spill_head;
-                const unsigned long long want = (unsigned long long)__popc(needm);
-                for (int tries = 0; tries < 4 && head < tail; ++tries) {
-                    const unsigned long long kk = (tail - head < want) ? tail - head : want;
-                    const unsigned long long got = atomicCAS(&a.ctl->spill_head, head, head + kk);
-                    if (got == head) {
-                        base = head;
-                        k = (int)kk;
-                        status = 1;
-                        break;
-                    }
-                    head = got;
-                }
-                if (status == 1) {
-                    level = 0;
-                } else if (head >= tail && (dynamic || alive == 0)) {
-                    status = -1;
-                } else if (!dynamic) {
-                    backoff = 1 << level;
-                    if (level < 6) ++level;
-                }
-            }
-        }
-        // every lane takes part in the broadcasts before any lane returns
-        status = __shfl_sync(FULL, status, 0);
-        k = __shfl_sync(FULL, k, 0);
-        base = __shfl_sync(FULL, base, 0);
-        if (!need) return 0;
-        if (status < 0) return -1;
-        if (status == 0) return 0;
-        const int rank = __popc(needm & ((1u << gbase) - 1u));
-        if (rank >= k) return 0;
-        // Each granted position's entry is written right after its producer
-        // reserved it.  The group leader waits for it (bounded), takes it and
-        // clears the slot, then hands it to its group.
-        uint32_t val = 0;
-        if (lane == gbase) {
-            volatile uint32_t *slot = (volatile uint32_t *)&a.spq[(base + rank) & kSpillQueueMask];
-            for (int spin = 0; spin < kEntrySpinLimit; ++spin) {
-                val = *slot;
-                if (val) break;
-                __nanosleep(64);
-            }
-            if (val) {
-                *slot = 0u;
-            } else {
-                volatile uint32_t *d = a.done;
-                d[2 * a.n_slots] = 1u;  // error word: an entry never appeared
-                __threadfence_system();
-            }
-        }
-        val = __shfl_sync(gm, val, gbase);
-        if (val == 0) {
-            failed = true;
-            return -1;
-        }
-        const uint32_t entry = val - 1u;
-        task = entry & 0xffffffu;
-        gj = &a.slot_jobs[entry >> 24];
-        return 1;
-    }
-    __device__ __forceinline__ void idle() { __nanosleep(2000); }
-    __device__ __forceinline__ bool aborted() const
-    {
-        return *(volatile const unsigned int *)&a.ctl->abort != 0u;
-    }
-    __device__ __forceinline__ Ext open(const Job *gj, uint32_t task, Scoring &sc)
-    {
-        const Job J = ldcg_job(gj);
-        sc = J.sc;
-        return decode_cg(J, task);
-    }
-    __device__ __forceinline__ void retire(const Job *gj, uint32_t task, bool overflow, int32_t T,
-                                           int32_t bi, int32_t bj)
-    {
-        const Job J = ldcg_job(gj);
-        if (overflow) {
-            serve_list_wide(a, gj, J, task);
-        } else {
-            store_result_cg(J, task, T, bi, bj);
-            serve_count(a, gj, J);
-        }
-    }
-};
-
-template <int L1, int C1, int L2, int C2>
-__global__ void __launch_bounds__(256)
-serve_kernel(ServeArgs a, const uint32_t *pk, int64_t nw)
-{
-    const unsigned warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp_global % kSpillWarpEvery == kSpillWarpEvery - 1) {
-        SpillSrc src{a, 0, 0, false, false};  // second tier for the kernel's whole life
-        lockstep_loop<L2, C2>(src, pk, nw);
-        return;
-    }
-    for (;;) {
-        RingSrc src{a, 0ull, 0, 0, false};
-        lockstep_loop<L1, C1>(src, pk, nw);
-        if (__any_sync(FULL, src.leaving || src.aborted())) break;
-        // The second-tier backlog grew: drain it with the wider tile, then
-        // go back to the ring.
-        SpillSrc help{a, 0, 0, true, false};
-        lockstep_loop<L2, C2>(help, pk, nw);
-        if (__any_sync(FULL, help.failed || help.aborted())) break;
-    }
-    __threadfence();  // this warp's queue pushes before it counts itself out
-    if ((threadIdx.x & 31) == 0) atomicSub(&a.ctl->ring_alive, 1u);
-}
-
-// Warps of a serving grid that run the first tier.
-__host__ __device__ inline uint32_t serve_ring_warps(int grid)
-{
-    const uint32_t total = (uint32_t)grid * 8u;
-    return total - total / kSpillWarpEvery;
-}
-
 template <int L, int C>
 __global__ void __launch_bounds__(256)
 lockstep_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_ptr,

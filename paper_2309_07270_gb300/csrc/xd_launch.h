@@ -36,6 +36,7 @@ cudaError_t launch_persistent(Tile t, int grid, const Job *jp, const uint32_t *o
 cudaError_t launch_spill(Tile t, bool count, int grid, const Job *jp, Spill in, Spill out,
                          cudaStream_t s);
 // Blocks per SM of a persistent tile at 256 threads per block.
+int persistent_block_threads(Tile t);  // threads per block of the persistent first tier
 int persistent_blocks_per_sm(Tile t);
 // Whether a scoring fits the packed 16-bit tiles exactly.
 bool packed_scoring_ok(const Scoring &sc);

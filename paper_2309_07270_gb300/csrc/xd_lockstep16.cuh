@@ -83,6 +83,18 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 
 __host__ __device__ inline uint32_t pack2(int32_t v) { return ((uint32_t)v & 0xFFFFu) * 0x10001u; }
 
+// a * one + b with one == 1 at run time: the same value as a + b (and as
+// a << s for one << s), issued as a multiply-add on the FMA pipe.  Every DPX,
+// byte-permute, logic and min/max instruction of the loop issues on the ALU
+// pipe, which bounds it; the compiler would issue these adds and shifts there
+// too.  `one` is a kernel argument, so the compiler cannot fold the multiply.
+__device__ __forceinline__ uint32_t fma_add(uint32_t a, uint32_t one, uint32_t b)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(one), "r"(b));
+    return r;
+}
+
 // Byte-permute selector giving 0xFFFF in the low half where slot t's match
 // bit is set and likewise in the high half for slot t+C2.  Match bits sit
 // at the msb of byte (s >> 2) of R[s & 3] (see dp16); msb-replicating
@@ -144,10 +156,12 @@ __device__ __forceinline__ bool live_hi(uint32_t v) { return (int32_t)v >= 0; }
 template <int C2, bool ODD, bool MASKED>
 __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
                                         uint32_t edge, uint32_t eq7, uint32_t ma2, uint32_t mi2,
-                                        uint32_t nthr2, uint32_t lo1_2, uint32_t nhi1_2)
+                                        uint32_t nthr2, uint32_t lo1_2, uint32_t nhi1_2,
+                                        uint32_t one)
 {
     // R[q]: the match bit of slot 4b + q at the msb of byte b
-    const uint32_t R[4] = {eq7 << 6, eq7 << 4, eq7 << 2, eq7};
+    const uint32_t R[4] = {fma_add(eq7, one << 6, 0u), fma_add(eq7, one << 4, 0u),
+                           fma_add(eq7, one << 2, 0u), eq7};
     uint32_t key[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) {
@@ -156,7 +170,7 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
         else sh = (t > 0) ? U[t - 1] : prmt(edge, U[C2 - 1], 0x5432);
         const uint32_t mk = prmt(R[t & 3], R[t & 3], mask_sel<C2>(t));
         const uint32_t s2 = (mk & ma2) | (~mk & mi2);
-        uint32_t r = __vimax3_s16x2(V[t] + s2, U[t], sh);  // carry-free add (header)
+        uint32_t r = __vimax3_s16x2(fma_add(V[t], one, s2), U[t], sh);  // carry-free add (header)
         if (MASKED) {
             // slot s lies in the rectangle iff lo <= s <= hi (lo = j0 - n,
             // hi = m - i0): max(s - hi - 1, lo - 1 - s) < 0, per half
@@ -166,7 +180,7 @@ __device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C
             r = (r & in) | (kDead2 & ~in);
         }
         // 16*(r - thr) + (S-1-slot), floored at -16: negative iff pruned
-        const uint32_t k = __viaddmax_s16x2(r, idx2<C2>(t) + nthr2, 0xFFF0FFF0u);
+        const uint32_t k = __viaddmax_s16x2(r, fma_add(nthr2, one, idx2<C2>(t)), 0xFFF0FFF0u);
         const uint32_t pm = prmt(k, k, 0xBB99);  // 0xFFFF where pruned
         V[t] = (r & ~pm) | (kDead2 & pm);
         key[t] = k;
@@ -196,8 +210,10 @@ __host__ __device__ inline int32_t rebase_step16(const Scoring &sc)
     return k;
 }
 
+// one: 1 (see fma_add).
 template <int L, int C2, class Src>
-__device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, int64_t nw)
+__device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, int64_t nw,
+                                                uint32_t one)
 {
     using namespace p16;
     constexpr int S = 2 * C2;  // slots per lane
@@ -284,11 +300,11 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         if (ODD) {
             uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
             if (top_lane) edge = kDead2;
-            lkey = dp16<C2, true, MASKED>(O, E, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2);
+            lkey = dp16<C2, true, MASKED>(O, E, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2, one);
         } else {
             uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
             if (bot_lane) edge = kDead2;
-            lkey = dp16<C2, false, MASKED>(E, O, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2);
+            lkey = dp16<C2, false, MASKED>(E, O, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2, one);
         }
         // Group key: value above lane above slot in lane, so one max finds
         // the lowest window slot among the cells holding the maximum.
@@ -502,39 +518,17 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
 }
 
 // Batched form of the packed kernel (same task source as lockstep_kernel).
+// 128-thread blocks: with the FMA-pipe adds the loop holds about 85
+// registers, five such blocks fit an SM (20 warps), and that measured faster
+// than capping the registers for more warps.
+constexpr int kPackedThreads = 128;
 template <int L, int C2>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPackedThreads)
 lockstep16_kernel(const Job *jp, const uint32_t *order, const uint32_t *n_tasks_ptr,
-                  uint32_t *counter, Spill spill)
+                  uint32_t *counter, Spill spill, uint32_t one)
 {
     BatchSrc src{jp, order, *n_tasks_ptr, counter, spill};
-    lockstep16_loop<L, C2>(src, jp->packed, jp->n_words);
-}
-
-// Serving form: ring warps run the packed tile, the spill warps (one warp
-// in kSpillWarpEvery, plus ring warps that help when the second-tier
-// backlog grows) the 32-bit tile L2 x C2, which also takes every task
-// whose scoring does not fit 16 bits.  Same protocol as serve_kernel.
-template <int L1, int C2a, int L2, int C2>
-__global__ void __launch_bounds__(256, (L1 * 2 * C2a <= 64) ? 3 : 2)
-serve16_kernel(ServeArgs a, const uint32_t *pk, int64_t nw)
-{
-    const unsigned warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp_global % kSpillWarpEvery == kSpillWarpEvery - 1) {
-        SpillSrc src{a, 0, 0, false, false};
-        lockstep_loop<L2, C2>(src, pk, nw);
-        return;
-    }
-    for (;;) {
-        RingSrc src{a, 0ull, 0, 0, false};
-        lockstep16_loop<L1, C2a>(src, pk, nw);
-        if (__any_sync(FULL, src.leaving || src.aborted())) break;
-        SpillSrc help{a, 0, 0, true, false};
-        lockstep_loop<L2, C2>(help, pk, nw);
-        if (__any_sync(FULL, help.failed || help.aborted())) break;
-    }
-    __threadfence();  // this warp's queue pushes before it counts itself out
-    if ((threadIdx.x & 31) == 0) atomicSub(&a.ctl->ring_alive, 1u);
+    lockstep16_loop<L, C2>(src, jp->packed, jp->n_words, one);
 }
 
 }  // namespace xd

@@ -33,7 +33,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "xd_device.cuh"
+#include "xd_serve_kernels.cuh"
 #include "xd_serve.h"
 #include "xdrop.h"
 
@@ -203,7 +203,7 @@ cudaError_t Server::ensure_kernel()
         if (q != cudaSuccess) return q;
         kernel_running = false;
     }
-    h_ctl_init->ring_alive = serve_ring_warps(grid);
+    h_ctl_init->ring_alive = serve_warps(grid);
     cudaError_t e = cudaMemcpyAsync(&d_ctl->ring_alive, &h_ctl_init->ring_alive, sizeof(unsigned int),
                                     cudaMemcpyHostToDevice, s_kernel);
     if (e == cudaSuccess)
@@ -220,6 +220,8 @@ cudaError_t Server::ensure_kernel()
     a.slot_jobs = d_jobs;
     a.done = d_done;
     a.n_slots = kSlots;
+    a.max_helpers = std::max<uint32_t>(1u, serve_warps(grid) / 4);  // a quarter of the warps
+    a.one = 1u;
     if (e == cudaSuccess) e = launch_serve(tile, grid, a, rr.packed, rr.n_words, s_kernel);
     if (e == cudaSuccess) {
         kernel_running = true;
@@ -261,6 +263,11 @@ bool Server::admit(Req *r)
     }
     char *d = d_arena + r->dev_off;
     char *h = h_pool + r->host_off;
+    // Clear the slot's done word before anything of this request can reach
+    // the device: a small request may finish (and the kernel write its tag)
+    // before this thread runs again after queueing the copies below.
+    h_done[2 * slot] = 0;
+    h_done[2 * slot + 1] = 0;
     memcpy(h + r->h_pairs, r->pairs.data(), r->n * sizeof(xdrop_pair));
     // Ring entries longest extension first (the batched form's order), so
     // the lockstep groups of a warp run extensions of similar length.
@@ -325,7 +332,6 @@ bool Server::admit(Req *r)
         fatal = std::string("serve admission: ") + cudaGetErrorString(e);
         return false;
     }
-    h_done[2 * slot] = 0;
     slots[slot] = r;
     r->slot = slot;
     r->state = ADMITTED;
@@ -623,6 +629,26 @@ int server_sync(Server *s, uint64_t ticket, int64_t timeout_ns, std::string &err
         s->cv.wait(lk, pred);
     } else if (!s->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred)) {
         err = "serving request not done";
+        if (r->state == ADMITTED) {
+            // what the device has: finished extensions and the slot's done word
+            uint32_t ctr[2] = {0, 0};
+            const char *d = s->d_arena + r->dev_off;
+            if (cudaMemcpyAsync(ctr, d + r->d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost,
+                                s->s_copy) == cudaSuccess &&
+                cudaStreamSynchronize(s->s_copy) == cudaSuccess) {
+                err += ": " + std::to_string(ctr[0]) + " of " + std::to_string(2 * r->n) +
+                       " extensions finished on the device, " + std::to_string(ctr[1]) +
+                       " listed for the wide pass; done word " +
+                       std::to_string(s->h_done[2 * r->slot]) + ", tag " + std::to_string(r->id);
+            }
+            ServeCtl c{};
+            if (cudaMemcpyAsync(s->h_ctl_snap, s->d_ctl, sizeof(ServeCtl), cudaMemcpyDeviceToHost,
+                                s->s_copy) == cudaSuccess &&
+                cudaStreamSynchronize(s->s_copy) == cudaSuccess) {
+                c = *s->h_ctl_snap;
+                err += "; surplus counts " + std::to_string(c.surplus_counts);
+            }
+        }
         return XDROP_ETIMEDOUT;
     }
     const int rc = r->rc;
@@ -649,6 +675,8 @@ ServerStats server_stats(Server *s)
         st.spill_taken = c.spill_head;
         st.ring_warps = c.ring_alive;
         st.idle_exits = c.idle_exits;
+        st.help_sessions = c.help_sessions;
+        st.surplus_counts = c.surplus_counts;
     }
     return st;
 }

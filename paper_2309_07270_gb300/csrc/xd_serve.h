@@ -29,6 +29,8 @@ struct ServerStats {
     uint64_t admission_waits = 0;
     uint64_t published = 0, consumed = 0, spill_reserved = 0, spill_taken = 0, ring_warps = 0;
     uint64_t idle_exits = 0;    // first-tier warps that left on the idle bound (all launches)
+    uint64_t help_sessions = 0; // warps that registered to serve the second tier (all launches)
+    uint64_t surplus_counts = 0; // extensions counted past their request's total (stays 0)
 };
 
 class Server;

@@ -1,7 +1,7 @@
 // Band tiles of width 128 (X up to about 100 with unit scores); the plain
 // per-batch kernel uses the 32 x 4 tile.
 #include "xd_launch.h"
-#include "xd_device.cuh"
+#include "xd_serve_kernels.cuh"
 
 namespace xd {
 
@@ -45,7 +45,7 @@ int occupancy_mid(Tile t)
 cudaError_t launch_spill_mid(int grid, const Job *jp, Spill in, Spill out, cudaStream_t s)
 {
     (void)cudaGetLastError();
-    window_spill_kernel<16, 8, false><<<grid, 256, 0, s>>>(jp, in, out);
+    window_spill_kernel<32, 4, false><<<grid, 256, 0, s>>>(jp, in, out);
     return cudaGetLastError();
 }
 

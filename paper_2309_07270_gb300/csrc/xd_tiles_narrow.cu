@@ -1,6 +1,6 @@
 // Band tiles of width 64 (X around 50 with unit scores).
 #include "xd_launch.h"
-#include "xd_device.cuh"
+#include "xd_serve_kernels.cuh"
 
 namespace xd {
 

@@ -2,7 +2,7 @@
 // (width 32, narrow bands such as x = 15), 4x16 and 8x8 (width 64), 8x16
 // and 16x8 (width 128).
 #include "xd_launch.h"
-#include "xd_lockstep16.cuh"
+#include "xd_serve_kernels.cuh"
 
 namespace xd {
 
@@ -11,7 +11,7 @@ static cudaError_t packed_impl(int grid, const Job *jp, const uint32_t *order, c
                                uint32_t *ctr, Spill sp, cudaStream_t s)
 {
     (void)cudaGetLastError();
-    lockstep16_kernel<L, C2><<<grid, 256, 0, s>>>(jp, order, n, ctr, sp);
+    lockstep16_kernel<L, C2><<<grid, kPackedThreads, 0, s>>>(jp, order, n, ctr, sp, 1u);
     return cudaGetLastError();
 }
 
@@ -19,7 +19,7 @@ template <int L, int C2>
 static int packed_occupancy_impl()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lockstep16_kernel<L, C2>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lockstep16_kernel<L, C2>, kPackedThreads, 0);
     return b;
 }
 
@@ -53,6 +53,8 @@ int occupancy_packed(Tile t)
 }
 
 bool packed_scoring_ok(const Scoring &sc) { return packed16_ok(sc); }
+
+int persistent_block_threads(Tile t) { return t.packed ? kPackedThreads : 256; }
 
 template <int L1, int C2a, int L2, int C2>
 static cudaError_t serve16_impl(int grid, const ServeArgs &a, const uint32_t *pk, int64_t nw,

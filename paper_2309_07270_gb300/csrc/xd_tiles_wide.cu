@@ -213,7 +213,7 @@ cudaError_t launch_spill(Tile t, bool count, int grid, const Job *jp, Spill in, 
                          cudaStream_t s)
 {
     if (t.lanes == 32 && t.c == 16) return launch_spill_512(count, grid, jp, in, out, s);
-    if (!count && t.lanes == 16 && t.c == 8) return launch_spill_mid(grid, jp, in, out, s);
+    if (!count && t.lanes == 32 && t.c == 4) return launch_spill_mid(grid, jp, in, out, s);
     return cudaErrorInvalidValue;
 }
 

@@ -47,21 +47,6 @@ struct Job {
     uint32_t tag;
 };
 
-// Control block of the serving kernel (device memory).  The host-written,
-// read-mostly words share one line; each device-hot counter has its own.
-struct ServeCtl {
-    unsigned long long published;   // ring entries the host has published (host writes)
-    unsigned long long idle_ns;     // a waiting warp leaves after this long (hang guard)
-    unsigned int stop;              // host: leave once idle
-    unsigned int yield;             // host: take no more tasks, leave when drained
-    unsigned int ring_alive;        // first-tier warps still running (host sets)
-    unsigned int abort;             // host: leave now, abandoning tasks (teardown)
-    unsigned int idle_exits;        // first-tier warps that left on the idle bound
-    alignas(128) unsigned long long consumed;    // ring entries taken (device CAS)
-    alignas(128) unsigned long long spill_tail;  // second-tier queue: entries reserved
-    alignas(128) unsigned long long spill_head;  // second-tier queue: entries taken
-};
-
 // Overflow hand-off between tiers.
 struct Spill {
     uint32_t *list;   // task ids

@@ -114,6 +114,7 @@ class Result:
                 "p99_ms": _percentile(self.latencies, 99) * 1e3 if self.latencies else None,
                 "mean_ms": statistics.mean(self.latencies) * 1e3 if self.latencies else None,
                 "errors": len(self.errors),
+                "first_errors": self.errors[:3],
                 "serve_stats": self.serve_stats}
 
 

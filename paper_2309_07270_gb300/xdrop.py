@@ -74,7 +74,9 @@ class ServeStats(ctypes.Structure):
                 ("admission_waits", ctypes.c_uint64), ("published", ctypes.c_uint64),
                 ("consumed", ctypes.c_uint64), ("spill_reserved", ctypes.c_uint64),
                 ("spill_taken", ctypes.c_uint64), ("ring_warps", ctypes.c_uint64),
-                ("idle_exits", ctypes.c_uint64)]
+                ("idle_exits", ctypes.c_uint64),
+                ("help_sessions", ctypes.c_uint64),
+                ("surplus_counts", ctypes.c_uint64)]
 
 
 class KmerParams(ctypes.Structure):

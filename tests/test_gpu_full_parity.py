@@ -133,8 +133,60 @@ def test_genome_29x_served_every_pair(X, oracle_full, genome29):
     assert not errors, errors
     assert st["requests_done"] == len(reqs)
     assert st["max_in_flight"] > 1
+    # every published extension was claimed (per block, with this backlog), and the
+    # overflowed ones were served by warps that left the first tier to help
+    assert st["consumed"] == st["published"]
+    assert st["spill_taken"] == st["spill_reserved"] > 0
+    assert st["help_sessions"] > 0
+    assert st["surplus_counts"] == 0
     for idx, out in zip(reqs, outs):
         assert_every_pair(out, want[idx], "served request")
+
+
+def test_ring_reuse_under_a_deep_backlog(X, oracle_full, genome29):
+    """Requests whose extensions outnumber the serving task ring (2^21
+    entries) several times, submitted at once by 8 producers: the ring is
+    reused while a deep backlog of claimed and unclaimed entries is in
+    flight, and requests finish out of order.  Every record equals the
+    oracle's, every extension is counted exactly once, and no slot reuse
+    loses or repeats a task."""
+    w = genome29.with_x(50)
+    want, _ = oracle_full(("genome29x", 50), w)
+    rng = np.random.default_rng(909)
+    reqs = [rng.choice(w.n_pairs, size=int(rng.integers(15_000, 20_001)), replace=False)
+            for _ in range(160)]
+    assert 2 * sum(len(r) for r in reqs) > 2.5 * (1 << 21)
+    sc = X.scoring(1, -1, -1, 50)
+    ctx = X.xdrop_init(0, 0, X.XDROP_MODE_SERVE)
+    outs = [np.zeros(len(idx), X.RESULT_DTYPE) for idx in reqs]
+    errors = []
+    try:
+        X.xdrop_load_reads(ctx, w.packed, w.read_off, w.read_len)
+
+        def producer(items):
+            try:
+                tickets = [X.xdrop_submit_pairs(ctx, w.pairs[reqs[i]], sc, outs[i]) for i in items]
+                for t in tickets:
+                    X.xdrop_sync(ctx, t, int(300e9))
+            except Exception as e:  # reported below
+                errors.append(e)
+
+        th = [threading.Thread(target=producer, args=(list(range(p, len(reqs), 8)),))
+              for p in range(8)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(timeout=900)
+        st = X.xdrop_get_serve_stats(ctx)
+    finally:
+        X.xdrop_free(ctx)
+    assert not errors, errors
+    assert st["requests_done"] == len(reqs)
+    assert st["published"] == st["consumed"] == 2 * sum(len(r) for r in reqs)
+    assert st["surplus_counts"] == 0
+    assert st["spill_taken"] == st["spill_reserved"]
+    for idx, out in zip(reqs, outs):
+        assert_every_pair(out, want[idx], "request after ring reuse")
 
 
 def test_uneven_1m_every_pair(X, oracle_full, uneven1m):

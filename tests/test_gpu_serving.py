@@ -218,6 +218,9 @@ def test_mixed_scorings_packed_and_not(X, orc, pool):
         X.xdrop_free(ctx)
     assert not errors, errors
     assert st["spill_taken"] > 0  # the second tier ran the unpacked scoring
+    # no warp is reserved for the second tier: ring warps registered to serve it
+    assert st["help_sessions"] > 0
+    assert st["spill_taken"] == st["spill_reserved"]
     for i, (p, idx) in enumerate(reqs):
         want = orc.align_pairs(pool.packed, pool.read_off, pool.read_len, pool.pairs[idx],
                                *scs[p % 2], nthreads=8)
