@@ -6,24 +6,37 @@
 //   match - gap <= 128, mismatch >= -128, mismatch + 2|gap| >= 0,
 //   x + match <= 1536.
 //
-// Normalised scores.  A cell on anti-diagonal d holds
-//   r = H + x + d*|gap| - B          (B: the rebase steps taken off)
-// stored as 16*r.  Then the two gap predecessors enter unchanged and the
-// diagonal one with s + 2|gap| >= 0:
+// Biased, normalised scores.  A live cell on anti-diagonal d holds
+//   r = H + x + d*|gap| - B + beta     (B: the rebase steps taken off,
+//                                       beta = match + |gap| + 1)
+// stored as 16*r in an unsigned half; a pruned cell holds 0.  The two gap
+// predecessors enter unchanged and the diagonal one with s + 2|gap| >= 0:
 //   r(d) = max(r_diag(d-2) + s + 2|gap|,  r_up(d-1),  r_left(d-1)),
-// one plain 32-bit add (both halves at once, see below) and one DPX
-// three-way max per register (two cells).  The threshold of diagonal d
-// (T of d-1 minus x) becomes thr = T + d*|gap| - B, a cell is live iff
-// r >= thr, and r - thr <= x + match.
+// one 32-bit add (both halves at once, see below) and one u16x2 three-way
+// max per register (two cells).  The X-drop threshold of diagonal d (T of
+// d-1 minus x) becomes thr = T + d*|gap| - B + beta, a cell is live iff
+// r >= thr, and r - thr <= x + match.  Every threshold is at least
+// match + 2|gap| + 1, so a pruned predecessor (0, or 16*(s + 2|gap|) after
+// the diagonal add) can never lift a cell to its threshold: a cell with no
+// live predecessor stays pruned, and one with a live predecessor takes the
+// same maximum as the recurrence over live predecessors.
 //
-// Key.  One more 32-bit add and a DPX add-max give each slot's key
-//   16*(r - thr) + (S-1-slot), floored at -16,
-// which is negative exactly for the cells the X-drop test prunes (their
-// stored value becomes kDead by the key's sign mask) and, for live cells,
+// Key.  One more 32-bit add gives each slot's key
+//   0x8000 + 16*(r - thr) + (S-1-slot),
+// which has bit 15 set exactly for the live cells (a byte permute spreads
+// that bit into the mask that zeroes the pruned ones) and, for live cells,
 // orders by value and then by lowest slot.  The lane's best key becomes
-// (key >> 4) * 512 + (31 - lane) * 16 + (key & 15) in 32 bits, so one
-// group max gives the largest value and, among equal values, the lowest
-// window slot: the first cell in order of increasing i on the diagonal.
+// value * 512 + (31 - lane) * 16 + (key & 15) in 32 bits, value = key/16 -
+// 0x800, so one group max gives the largest value and, among equal values,
+// the lowest window slot: the first cell in order of increasing i on the
+// diagonal.
+//
+// Substitution.  The match bits of the lane's 16 slots come from one XOR of
+// the 2-bit base windows.  For register t the two bits (slots t and t+C2)
+// are moved to bits p and p+16, p = 13 or 15, by a left shift (a multiply
+// on the FMA pipe) and masked; a high multiply by 16 (match - mismatch) *
+// 2^(32-p) turns them into the per-half match bonus, and its addend is the
+// mismatch substitution.  One ALU instruction (the mask) per register.
 //
 // Layout.  Lane g of a group of L lanes holds the window slots g*S .. g*S+S-1
 // (S = 2*C2 slots).  Register t holds slot t in its low half and slot t+C2
@@ -31,34 +44,31 @@
 // register t sits in register t+1 (t-1) at the same half; only the end
 // registers need a byte permute and one shuffle per diagonal.
 //
-// Ranges, in units of r, with kR the rebase step of the scoring
-// (rebase_step16, between 128 and 1792 inside the range above).  After
-// every pair of diagonals (odd d-1, even d) the frame is rebased by kR
-// once thr of d-1 reaches kR.  Every live value of d-1 and d is at least
-// that threshold, so live values stay >= 0 (>= thr >= 0) at all times and
-// pruned ones hold kDead = -256.  thr grows by at most 3|gap| + 2 match
-// over the three diagonals between two tests, so thr < kR + 3|gap| +
-// 2 match <= 1666 and every live value is at most thr + x + match <= 2047
-// (16 times that fits a signed half).  A value built from a pruned
-// predecessor stays below -256 + 255 < 0 <= thr.  No value formed is
-// below kDead (substitutions are >= 0 here), the lowest key sum is
-// 16 kDead/16 - 16 * 1666 > -32768, and a rebase takes kDead to
-// kDead - 16 kR >= -32768 before the floor restores it.
+// Ranges, in units of r, with kR = 2040 - 3 match - 3|gap| the rebase step
+// (rebase_step16: at least 1656 inside the range above, and at least
+// match + 2|gap|, the most one pair of diagonals can raise a threshold).
+// After every pair of diagonals (odd d-1, even d) the frame is rebased by
+// kR once thr of d-1 reaches kR + match + 1.  Every live value of d-1 and d
+// is at least that threshold, so it stays above match + 1 > 0 after the
+// rebase, and the next threshold is again at least match + 2|gap| + 1.
+// thr grows by at most 3|gap| + 2 match over the three diagonals between
+// two tests, so thr <= 2040 always (16 thr < 0x8000: the key's pruned
+// range stays non-negative) and every live value is at most
+// thr + x + match <= 3576 (16 times that < 2^16).
 //
-// Carry-free adds.  V + s2 (stored value plus packed substitution, s2 in
-// [0, 16*255]) and idx + (-16 thr) (idx <= 15 < 16 thr unless thr = 0) are
-// plain 32-bit adds: the low halves, read unsigned, never reach 2^16 (a
-// live half is < 2^15 - s2, kDead is 0xF000 and 0xF000 + 0x0FF0 < 2^16),
-// so nothing carries into the high half.
+// Carry-free adds.  V + s2 (stored value plus packed substitution, s2 <=
+// 16*256), z + idx (z = 0x8000 - 16 thr per half) and r + (z + idx) are
+// plain 32-bit adds: by the ranges above no low half, read unsigned,
+// reaches 2^16, so nothing carries into the high half.
 //
-// Window edges.  Live values are >= 0 and pruned ones negative, so the
-// sign bit of a half tells whether that slot is live.  The edges are
-// tested once per pair of diagonals, after the even one: no live cell of
-// diagonals d+1, d+2 can leave the window unless E's top slot (diagonal d)
-// or O's top slot (d-1) is live, or E's bottom slot is.  The window then
-// shifts up one slot if E's two bottom slots and O's bottom slot are dead,
-// or down one slot if the two top slots of E and of O are dead; otherwise
-// the band has outgrown the window and the task goes to a wider tier.
+// Window edges.  Live values are > 0 and pruned ones 0, so a half is live
+// iff it is nonzero.  The edges are tested once per pair of diagonals,
+// after the even one: no live cell of diagonals d+1, d+2 can leave the
+// window unless E's top slot (diagonal d) or O's top slot (d-1) is live,
+// or E's bottom slot is.  The window then shifts up one slot if E's two
+// bottom slots and O's bottom slot are dead, or down one slot if the two
+// top slots of E and of O are dead; otherwise the band has outgrown the
+// window and the task goes to a wider tier.
 #pragma once
 #include <stdint.h>
 
@@ -70,9 +80,8 @@ namespace xd {
 
 namespace p16 {
 
-constexpr int32_t kScale = 16;            // stored value = 16 * r
-constexpr int32_t kDead = -256 * kScale;  // stored value of a pruned slot
-constexpr uint32_t kDead2 = 0xF000F000u;  // kDead in both halves
+constexpr int32_t kScale = 16;       // stored value = 16 * r
+constexpr uint32_t kKey2 = 0x80008000u;  // key offset in both halves: live iff bit 15
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 {
@@ -95,15 +104,12 @@ __device__ __forceinline__ uint32_t fma_add(uint32_t a, uint32_t one, uint32_t b
     return r;
 }
 
-// Byte-permute selector giving 0xFFFF in the low half where slot t's match
-// bit is set and likewise in the high half for slot t+C2.  Match bits sit
-// at the msb of byte (s >> 2) of R[s & 3] (see dp16); msb-replicating
-// selectors (8 | byte) turn them into half-word masks.
-template <int C2>
-__host__ __device__ constexpr uint32_t mask_sel(int t)
+// The high word of a * b, plus c (FMA pipe).
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
 {
-    return (uint32_t)((8 | (t >> 2)) | ((8 | (t >> 2)) << 4) | ((8 | ((t + C2) >> 2)) << 8) |
-                      ((8 | ((t + C2) >> 2)) << 12));
+    uint32_t r;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
 }
 
 template <int C2>
@@ -124,71 +130,80 @@ __host__ __device__ constexpr uint32_t nslot2(int t)
     return ((uint32_t)(-t) & 0xFFFFu) | (((uint32_t)(-(t + C2)) & 0xFFFFu) << 16);
 }
 
+// Register t's match bits: shifted left by 12 - 4 (t >> 1) they sit at
+// bits p and p + 16, p = 13 + 2 (t & 1) (see the header).
+__host__ __device__ constexpr int subst_shift(int t) { return 12 - 4 * (t >> 1); }
+__host__ __device__ constexpr uint32_t subst_mask(int t)
+{
+    return (1u << (13 + 2 * (t & 1))) | (1u << (29 + 2 * (t & 1)));
+}
+
 template <int N>
 __device__ __forceinline__ uint32_t tree_max2(const uint32_t (&k)[N])
 {
     if constexpr (N == 1) {
         return k[0];
     } else if constexpr (N == 2) {
-        return __vmaxs2(k[0], k[1]);
+        return __vmaxu2(k[0], k[1]);
     } else {
         constexpr int M = (N + 2) / 3;
         uint32_t r[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            if (3 * i + 2 < N) r[i] = __vimax3_s16x2(k[3 * i], k[3 * i + 1], k[3 * i + 2]);
-            else if (3 * i + 1 < N) r[i] = __vmaxs2(k[3 * i], k[3 * i + 1]);
+            if (3 * i + 2 < N) r[i] = __vimax3_u16x2(k[3 * i], k[3 * i + 1], k[3 * i + 2]);
+            else if (3 * i + 1 < N) r[i] = __vmaxu2(k[3 * i], k[3 * i + 1]);
             else r[i] = k[3 * i];
         }
         return tree_max2<M>(r);
     }
 }
 
-// A slot is live iff its half is non-negative (pruned slots hold kDead).
-__device__ __forceinline__ bool live_lo(uint32_t v) { return (v & 0x8000u) == 0; }
-__device__ __forceinline__ bool live_hi(uint32_t v) { return (int32_t)v >= 0; }
+// A slot is live iff its half is nonzero (pruned slots hold 0).
+__device__ __forceinline__ bool live_lo(uint32_t v) { return (v & 0xFFFFu) != 0; }
+__device__ __forceinline__ bool live_hi(uint32_t v) { return (v >> 16) != 0; }
 
 // One anti-diagonal for one lane: V (diagonal d-2, overwritten with d) and
 // U (d-1).  edge: the neighbouring lane's end register of U (next lane's
-// register 0 on odd diagonals, previous lane's register C2-1 on even ones).
-// eq7: bit 2s+1 set iff slot s's bases match.  Returns the lane's 16-bit
-// key, sign-extended.
+// register 0 on odd diagonals, previous lane's register C2-1 on even ones),
+// 0 beyond the group.  eq7: bit 2s+1 set iff slot s's bases match.  k13,
+// k15: 16 (match - mismatch) << 19 and << 17; mi2: the packed mismatch
+// substitution 16 (mismatch + 2|gap|); z: 0x8000 - 16 thr in both halves.
+// Returns the lane's largest key (0 .. 0xFFFF; below 0x8000 iff every slot
+// was pruned).
 template <int C2, bool ODD, bool MASKED>
-__device__ __forceinline__ int32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
-                                        uint32_t edge, uint32_t eq7, uint32_t ma2, uint32_t mi2,
-                                        uint32_t nthr2, uint32_t lo1_2, uint32_t nhi1_2,
-                                        uint32_t one)
+__device__ __forceinline__ uint32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
+                                         uint32_t edge, uint32_t eq7, uint32_t mi2,
+                                         uint32_t k13, uint32_t k15, uint32_t z,
+                                         uint32_t lo1_2, uint32_t nhi1_2, uint32_t one)
 {
-    // R[q]: the match bit of slot 4b + q at the msb of byte b
-    const uint32_t R[4] = {fma_add(eq7, one << 6, 0u), fma_add(eq7, one << 4, 0u),
-                           fma_add(eq7, one << 2, 0u), eq7};
+    static_assert(C2 == 4 || C2 == 8, "packed registers per lane");
+    // e: slot t's match bit at 2t+1, slot t+C2's at 2t+17
+    const uint32_t e = (C2 == 4) ? prmt(eq7, eq7, 0x2100) : eq7;
+    const uint32_t es[4] = {fma_add(e, one << 12, 0u), fma_add(e, one << 8, 0u),
+                            fma_add(e, one << 4, 0u), e};
     uint32_t key[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) {
         uint32_t sh;
         if (ODD) sh = (t + 1 < C2) ? U[t + 1] : prmt(U[0], edge, 0x5432);
         else sh = (t > 0) ? U[t - 1] : prmt(edge, U[C2 - 1], 0x5432);
-        const uint32_t mk = prmt(R[t & 3], R[t & 3], mask_sel<C2>(t));
-        const uint32_t s2 = (mk & ma2) | (~mk & mi2);
-        uint32_t r = __vimax3_s16x2(fma_add(V[t], one, s2), U[t], sh);  // carry-free add (header)
+        const uint32_t w = es[t >> 1] & subst_mask(t);
+        const uint32_t s2 = mad_hi(w, (t & 1) ? k15 : k13, mi2);
+        uint32_t r = __vimax3_u16x2(fma_add(V[t], one, s2), U[t], sh);  // carry-free (header)
         if (MASKED) {
             // slot s lies in the rectangle iff lo <= s <= hi (lo = j0 - n,
             // hi = m - i0): max(s - hi - 1, lo - 1 - s) < 0, per half
             const uint32_t c = __viaddmax_s16x2(nslot2<C2>(t), lo1_2, 0x80008000u);
             const uint32_t u = __viaddmax_s16x2(slot2<C2>(t), nhi1_2, c);
-            const uint32_t in = prmt(u, u, 0xBB99);  // 0xFFFF where inside
-            r = (r & in) | (kDead2 & ~in);
+            r &= prmt(u, u, 0xBB99);  // 0xFFFF where inside
         }
-        // 16*(r - thr) + (S-1-slot), floored at -16: negative iff pruned
-        const uint32_t k = __viaddmax_s16x2(r, fma_add(nthr2, one, idx2<C2>(t)), 0xFFF0FFF0u);
-        const uint32_t pm = prmt(k, k, 0xBB99);  // 0xFFFF where pruned
-        V[t] = (r & ~pm) | (kDead2 & pm);
+        // 0x8000 + 16*(r - thr) + (S-1-slot): bit 15 set iff live
+        const uint32_t k = fma_add(r, one, fma_add(z, one, idx2<C2>(t)));
+        V[t] = r & prmt(k, k, 0xBB99);
         key[t] = k;
     }
     const uint32_t kk = tree_max2<C2>(key);
-    const int32_t hi = (int32_t)kk >> 16;
-    const int32_t lo = (int32_t)prmt(kk, 0u, 0x9910);  // sign-extended low half
-    return hi > lo ? hi : lo;
+    return max(kk >> 16, kk & 0xFFFFu);
 }
 
 }  // namespace p16
@@ -200,14 +215,10 @@ __host__ __device__ inline bool packed16_ok(const Scoring &sc)
 }
 
 // Frame step of one rebase (units of r) for a scoring that passes
-// packed16_ok: at least 128 there (see the header comment's ranges).
+// packed16_ok: between 1656 and 2033 there (see the header comment's ranges).
 __host__ __device__ inline int32_t rebase_step16(const Scoring &sc)
 {
-    const int32_t ng = -sc.gap;
-    int32_t k = 1792;
-    k = k < 1667 - 3 * ng - 2 * sc.match ? k : 1667 - 3 * ng - 2 * sc.match;
-    k = k < 2048 - sc.x - 3 * sc.match - 3 * ng ? k : 2048 - sc.x - 3 * sc.match - 3 * ng;
-    return k;
+    return 2040 - 3 * sc.match + 3 * sc.gap;
 }
 
 // one: 1 (see fma_add).
@@ -224,6 +235,10 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     const int gbase = lane - glane;
     const unsigned gm = group_mask<L>(gbase);
     const bool bot_lane = glane == 0, top_lane = glane == L - 1;
+    // per-lane constants: 0/1 factors that clear the shuffled-in edge
+    // beyond the group, and the halves the window-edge test reads
+    const uint32_t keep_up = top_lane ? 0u : 1u, keep_dn = bot_lane ? 0u : 1u;
+    const uint32_t tmask = top_lane ? 0xFFFF0000u : 0u, bmask = bot_lane ? 0x0000FFFFu : 0u;
 
     // Per-group task state (uniform within a group).
     bool active = false, exhausted = false;
@@ -234,20 +249,21 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     int dir = 1;
     int32_t mn = 0, m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
     int32_t Q = 0;                      // frame offset: thr = T + Q
-    int32_t kR = 0;                     // rebase step
+    int32_t kR = 0, kRL = 0;            // rebase step, and the threshold that triggers one
     int32_t xup = 0;                    // (x + 1) * 512: a group key this large raises T
     int32_t bkey = 0, bi0 = 0, bd = 0;  // best cell: group key, this lane's i0, diagonal
     int32_t ng = 1;                     // |gap|
-    uint32_t ma2 = 0, mi2 = 0;          // packed 16 * (match / mismatch + 2|gap|)
+    uint32_t mi2 = 0;                   // packed 16 * (mismatch + 2|gap|)
+    uint32_t k13 = 0, k15 = 0;          // 16 (match - mismatch) << 19, << 17
     bool prev_dead = false, fin = false, rb = false;
     uint32_t E[C2], O[C2];
 #pragma unroll
-    for (int t = 0; t < C2; ++t) { E[t] = kDead2; O[t] = kDead2; }
+    for (int t = 0; t < C2; ++t) { E[t] = 0u; O[t] = 0u; }
     uint32_t Aw = 0, LA = 0, Bw = 0, LB = 0;
     int la_n = 16;        // warp-uniform: diagonal pairs the lookahead words still cover
     int32_t budget = 0;   // warp-uniform: diagonal pairs known to stay inside every rectangle
-    const int32_t lane_bits = (31 - glane) << 4;
-    const uint32_t dead16 = (uint32_t)kDead & 0xFFFFu;
+    // (31 - lane) * 16, less the key offset's share of the group key
+    const int32_t lane_bits = ((31 - glane) << 4) - (0x800 << 9);
 
     auto retire = [&](bool overflow) {
         if (bd > 0) {
@@ -285,7 +301,8 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             LB <<= 2;
         }
         thr = T + Q;
-        const uint32_t nthr2 = prmt((uint32_t)(-kScale * thr), 0u, 0x1010);
+        // 0x8000 - 16 thr in both halves (no borrow: 16 thr <= 0x8000)
+        const uint32_t z = (uint32_t)thr * 0xFFEFFFF0u + kKey2;
         // rectangle bounds of this lane's slots, clamped into 16 bits (only
         // the masked copy reads them)
         uint32_t lo1_2 = 0, nhi1_2 = 0;
@@ -296,19 +313,19 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         }
         const uint32_t xx = Aw ^ Bw;
         const uint32_t eq7 = ~(xx | (xx << 1));
-        int32_t lkey;
+        uint32_t lk;
         if (ODD) {
-            uint32_t edge = __shfl_down_sync(FULL, E[0], 1, L);
-            if (top_lane) edge = kDead2;
-            lkey = dp16<C2, true, MASKED>(O, E, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2, one);
+            const uint32_t edge = fma_add(__shfl_down_sync(FULL, E[0], 1, L), keep_up, 0u);
+            lk = dp16<C2, true, MASKED>(O, E, edge, eq7, mi2, k13, k15, z, lo1_2, nhi1_2, one);
         } else {
-            uint32_t edge = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
-            if (bot_lane) edge = kDead2;
-            lkey = dp16<C2, false, MASKED>(E, O, edge, eq7, ma2, mi2, nthr2, lo1_2, nhi1_2, one);
+            const uint32_t edge = fma_add(__shfl_up_sync(FULL, O[C2 - 1], 1, L), keep_dn, 0u);
+            lk = dp16<C2, false, MASKED>(E, O, edge, eq7, mi2, k13, k15, z, lo1_2, nhi1_2, one);
         }
         // Group key: value above lane above slot in lane, so one max finds
-        // the lowest window slot among the cells holding the maximum.
-        const int32_t mkey = lockstep_group_max<L>((lkey >> 4) * 512 + ((lkey & 15) | lane_bits));
+        // the lowest window slot among the cells holding the maximum.  With
+        // lk = 16 v + i: 32 lk - 31 i = 512 v + i (multiply-adds).
+        const int32_t mkey = lockstep_group_max<L>(
+            (int32_t)fma_add(lk, one << 5, fma_add(lk & 15u, 0u - 31u, (uint32_t)lane_bits)));
         if (mkey >= xup) {  // best value - thr > x: T rises (decoded at retire)
             T += (mkey >> 9) - sc.x;
             bkey = mkey;
@@ -332,11 +349,11 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         prev_dead = dead_e;
         --budget;
         --la_n;
-        rb = active && thr_o >= kR;
+        rb = active && thr_o >= kRL;
         // window edges: this group's bottom lane tests E's bottom slot, its
-        // top lane the top slots of E and O (sign bit set = pruned)
-        const uint32_t ew = top_lane ? (E[C2 - 1] & O[C2 - 1]) : (E[0] << 16);
-        const bool edge = active && (bot_lane || top_lane) && (int32_t)ew >= 0;
+        // top lane the top slots of E and O (a nonzero half is live)
+        const uint32_t ew = ((E[C2 - 1] | O[C2 - 1]) & tmask) | (E[0] & bmask);
+        const bool edge = active && ew != 0u;
         bool ev = edge || fin || rb || la_n == 0 || (!active && !exhausted);
         if (!MASKED) ev = ev || budget < 1;
         return __any_sync(FULL, ev);
@@ -370,7 +387,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             if (__any_sync(FULL, su)) {
                 uint32_t ne = __shfl_down_sync(FULL, E[0], 1, L);
                 uint32_t no = __shfl_down_sync(FULL, O[0], 1, L);
-                if (top_lane) { ne = kDead2; no = kDead2; }
+                if (top_lane) { ne = 0u; no = 0u; }
                 if (su) {
                     const uint32_t te = prmt(E[0], ne, 0x5432), to = prmt(O[0], no, 0x5432);
 #pragma unroll
@@ -384,7 +401,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             if (__any_sync(FULL, sd)) {
                 uint32_t pe = __shfl_up_sync(FULL, E[C2 - 1], 1, L);
                 uint32_t po = __shfl_up_sync(FULL, O[C2 - 1], 1, L);
-                if (bot_lane) { pe = kDead2; po = kDead2; }
+                if (bot_lane) { pe = 0u; po = 0u; }
                 if (sd) {
                     const uint32_t te = prmt(pe, E[C2 - 1], 0x5432);
                     const uint32_t to = prmt(po, O[C2 - 1], 0x5432);
@@ -412,13 +429,14 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
             la_n = 16;
         }
         // Every live value of the pair is >= 16 thr of its odd diagonal:
-        // once that threshold reaches kR, take kR off the frame.
+        // once that threshold reaches kR + match + 1, take kR off the frame
+        // (pruned halves stay 0; no half borrows).
         if (active && rb) {
-            const uint32_t mr = pack2(-kScale * kR);
+            const uint32_t mr = pack2(kScale * kR);
 #pragma unroll
             for (int t = 0; t < C2; ++t) {
-                E[t] = __viaddmax_s16x2(E[t], mr, kDead2);
-                O[t] = __viaddmax_s16x2(O[t], mr, kDead2);
+                E[t] = __vmaxu2(E[t], mr) - mr;
+                O[t] = __vmaxu2(O[t], mr) - mr;
             }
             Q -= kR;
         }
@@ -469,17 +487,22 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         mn = m + n;
                         ng = -sc.gap;
                         kR = rebase_step16(sc);
+                        kRL = kR + sc.match + 1;
                         xup = (sc.x + 1) * 512;
-                        ma2 = pack2(kScale * (sc.match + 2 * ng));
                         mi2 = pack2(kScale * (sc.mismatch + 2 * ng));
-                        // origin (H = 0) at window slot W/2, stored as 16 * (0 + x)
+                        k13 = (uint32_t)(kScale * (sc.match - sc.mismatch)) << 19;
+                        k15 = (uint32_t)(kScale * (sc.match - sc.mismatch)) << 17;
+                        // origin (H = 0) at window slot W/2, stored as
+                        // 16 * (x + beta), beta = match + |gap| + 1
+                        const int32_t beta = sc.match + ng + 1;
+                        const uint32_t orig = (uint32_t)(kScale * (sc.x + beta));
 #pragma unroll
                         for (int t = 0; t < C2; ++t) {
                             const int slo = glane * S + t, shi = slo + C2;
-                            const uint32_t lo = (slo == W / 2) ? (uint32_t)(kScale * sc.x) : dead16;
-                            const uint32_t hi = (shi == W / 2) ? (uint32_t)(kScale * sc.x) : dead16;
+                            const uint32_t lo = (slo == W / 2) ? orig : 0u;
+                            const uint32_t hi = (shi == W / 2) ? orig : 0u;
                             E[t] = lo | (hi << 16);
-                            O[t] = kDead2;
+                            O[t] = 0u;
                         }
                         i0 = -(W / 2) + glane * S;
                         j0 = (W / 2) - glane * S;
@@ -489,7 +512,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         LB = back16_u(pk, nw, sb0, dir, j0 + 16);
                         d = 0;
                         T = 0;
-                        Q = 0;
+                        Q = beta;
                         bi = 0;
                         bj = 0;
                         bd = 0;

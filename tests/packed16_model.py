@@ -3,19 +3,20 @@
 This is neither the oracle nor the CUDA path: it restates, in plain Python
 integers, the arithmetic that ``lockstep16_loop`` in
 ``paper_2309_07270_gb300/csrc/xd_lockstep16.cuh`` performs for one group of
-lanes (two window slots per 32-bit register, s16x2 max / add-max and plain
-32-bit adds of packed halves, byte permutes, the normalised and scaled
-frame, rebasing, the packed key, the window-edge test after every pair of
-diagonals and the window shifts), so that ``test_packed16_model.py`` can
-check on the CPU that this arithmetic reaches the oracle's result exactly,
-never wraps a 16-bit half and never carries from one half into the other.
-Any change to the kernel's arithmetic must be made here too.
+lanes (two window slots per 32-bit register, unsigned u16x2 max, plain
+32-bit adds and multiply-adds of packed halves, byte permutes, the biased
+and scaled frame in which a pruned slot holds 0, rebasing, the packed key,
+the substitution built from match bits by multiplication, the window-edge
+test after every pair of diagonals and the window shifts), so that
+``test_packed16_model.py`` can check on the CPU that this arithmetic
+reaches the oracle's result exactly, never wraps a 16-bit half and never
+carries from one half into the other.  Any change to the kernel's
+arithmetic must be made here too.
 """
 
 M32 = 0xFFFFFFFF
 SCALE = 16            # stored value = 16 * r
-DEAD = -256 * SCALE   # stored value of a pruned slot
-DEAD2 = 0xF000F000
+KEY0 = 0x8000         # key offset: a slot is live iff its key has bit 15 set
 
 
 class Wrap(AssertionError):
@@ -32,8 +33,19 @@ def halves(x):
     return s16(x), s16(x >> 16)
 
 
+def uhalves(x):
+    return x & 0xFFFF, (x >> 16) & 0xFFFF
+
+
 def mk(lo, hi):
     return ((lo & 0xFFFF) | ((hi & 0xFFFF) << 16)) & M32
+
+
+def umk(lo, hi):
+    for v in (lo, hi):
+        if not 0 <= v <= 0xFFFF:
+            raise Wrap(v)
+    return lo | (hi << 16)
 
 
 def prmt(a, b, sel):
@@ -50,7 +62,7 @@ def prmt(a, b, sel):
 
 
 def add2(a, b):
-    """DPX-style per-half add (no carry between halves); wrap is an error."""
+    """DPX-style per-half signed add (no carry between halves); wrap is an error."""
     la, ha = halves(a)
     lb, hb = halves(b)
     for v in (la + lb, ha + hb):
@@ -59,22 +71,35 @@ def add2(a, b):
     return mk(la + lb, ha + hb)
 
 
-def iadd32(a, b):
-    """A plain 32-bit add of two packed registers: exact per half only when
-    the low halves, read unsigned, do not carry and neither half wraps."""
-    if (a & 0xFFFF) + (b & 0xFFFF) > 0xFFFF:
-        raise Wrap("carry from the low half")
-    return add2(a, b)
+def uadd32(a, b):
+    """A plain 32-bit add (or multiply-add by one) of two packed registers:
+    exact per half only when neither half, read unsigned, reaches 2^16."""
+    la, ha = uhalves(a)
+    lb, hb = uhalves(b)
+    return umk(la + lb, ha + hb)
+
+
+def usub32(a, b):
+    """A plain 32-bit subtraction: exact per half only when no half borrows."""
+    la, ha = uhalves(a)
+    lb, hb = uhalves(b)
+    return umk(la - lb, ha - hb)
+
+
+def umax2(a, b):
+    la, ha = uhalves(a)
+    lb, hb = uhalves(b)
+    return umk(max(la, lb), max(ha, hb))
+
+
+def umax3(a, b, c):
+    return umax2(umax2(a, b), c)
 
 
 def max2(a, b):
     la, ha = halves(a)
     lb, hb = halves(b)
     return mk(max(la, lb), max(ha, hb))
-
-
-def max3(a, b, c):
-    return max2(max2(a, b), c)
 
 
 def addmax2(a, b, c):
@@ -94,15 +119,46 @@ def fits(match, mismatch, gap, x):
 def rebase_step(match, gap, x):
     """The frame step of one rebase (rebase_step16 in the kernel)."""
     ng = -gap
-    return min(1792, 1667 - 3 * ng - 2 * match, 2048 - x - 3 * match - 3 * ng)
+    return 2040 - 3 * match - 3 * ng
+
+
+def frame_bias(match, gap):
+    """The frame's offset at the origin (threshold of diagonal 1 minus |gap|):
+    every threshold is then at least match + 2|gap| + 1, so a pruned slot
+    (stored 0) can never feed a live cell."""
+    return match - gap + 1
+
+
+def rebase_margin(match):
+    """A rebase happens once the odd diagonal's threshold reaches kR plus this."""
+    return match + 1
 
 
 def live_lo(v):
-    return not v & 0x8000
+    return (v & 0xFFFF) != 0
 
 
 def live_hi(v):
-    return not v & 0x80000000
+    return (v >> 16) != 0
+
+
+# Substitution of register t from the match bits.  e holds slot t's match
+# bit at 2t+1 and slot t+C2's at 2t+17 (for C2 = 4 after one byte permute).
+# Shifted left by 12 - 4*(t >> 1), the two bits sit at p = 13 + 2*(t & 1)
+# and p + 16; a high multiply by dm * 2^(32-p), with dm = 16 (match -
+# mismatch) < 2^13, turns them into the per-half match bonus, and the
+# multiply-add's addend is the mismatch substitution.
+def substitution(eq7, t, C2, mi2, dm):
+    if C2 == 4:
+        e = prmt(eq7, eq7, 0x2100)  # bytes 0, 0, 1, 2: slot t+4 moves up by 8
+    else:
+        e = eq7
+    sh, p = 12 - 4 * (t >> 1), 13 + 2 * (t & 1)
+    src = (e << sh) & M32
+    w = src & ((1 << p) | (1 << (p + 16)))
+    K = dm << (32 - p)
+    assert K <= M32 and (w * K) & M32 == 0
+    return uadd32((w * K) >> 32, mi2)
 
 
 def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
@@ -119,11 +175,13 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
         stats.setdefault(k, 0)
     assert fits(match, mismatch, gap, x)
     C2, S = regs, 2 * regs
+    assert C2 in (4, 8)
     W = lanes * S
     m, n = len(a), len(b)
     ng = -gap
     kR = rebase_step(match, gap, x)
-    assert kR >= 128
+    kRL = kR + rebase_margin(match)
+    assert kR >= match + 2 * ng
 
     def base_a(i):  # 1-based; out-of-range positions get arbitrary codes
         return int(a[i - 1]) if 1 <= i <= m else (i * 7 + 1) & 3
@@ -131,18 +189,21 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
     def base_b(j):
         return int(b[j - 1]) if 1 <= j <= n else (j * 5 + 2) & 3
 
-    ma2 = pack2(SCALE * (match + 2 * ng))
     mi2 = pack2(SCALE * (mismatch + 2 * ng))
+    dm = SCALE * (match - mismatch)
     E = [[0] * C2 for _ in range(lanes)]
-    O = [[DEAD2] * C2 for _ in range(lanes)]
+    O = [[0] * C2 for _ in range(lanes)]
+    beta = frame_bias(match, gap)
+    origin = SCALE * (x + beta)
     for g in range(lanes):
         for t in range(C2):
-            lo = SCALE * x if g * S + t == W // 2 else DEAD
-            hi = SCALE * x if g * S + t + C2 == W // 2 else DEAD
-            E[g][t] = mk(lo, hi)
+            lo = origin if g * S + t == W // 2 else 0
+            hi = origin if g * S + t + C2 == W // 2 else 0
+            E[g][t] = umk(lo, hi)
     i0 = [-(W // 2) + g * S for g in range(lanes)]
     j0 = [(W // 2) - g * S for g in range(lanes)]
-    d = T = Q = 0
+    d = T = 0
+    Q = beta
     best = None  # (group key, window base i, diagonal)
     prev_dead = False
 
@@ -163,7 +224,9 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
             raise AssertionError("unmasked diagonal leaves the rectangle")
         V, U = (O, E) if odd else (E, O)
         thr = T + Q
-        nthr2 = pack2(-SCALE * thr)
+        if not match + 2 * ng + 1 <= thr <= 2048:
+            raise Wrap(("threshold", thr))
+        z = umk(KEY0 - SCALE * thr, KEY0 - SCALE * thr)  # 0x80008000 - 16 thr * 0x10001
         lane_keys = []
         newV = [list(v) for v in V]
         for g in range(lanes):
@@ -171,22 +234,18 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
             for s in range(16):
                 xx |= ((base_a(i0[g] + s) ^ base_b(j0[g] - s)) & 3) << (2 * s)
             eq7 = ~(xx | (xx << 1)) & M32  # bit 2s+1: slot s matches
-            R = [(eq7 << (6 - 2 * q)) & M32 for q in range(4)]
             if odd:
-                edge = U[g + 1][0] if g + 1 < lanes else DEAD2
+                edge = U[g + 1][0] if g + 1 < lanes else 0
             else:
-                edge = U[g - 1][C2 - 1] if g > 0 else DEAD2
+                edge = U[g - 1][C2 - 1] if g > 0 else 0
             keys = []
             for t in range(C2):
                 if odd:
                     sh = U[g][t + 1] if t + 1 < C2 else prmt(U[g][0], edge, 0x5432)
                 else:
                     sh = U[g][t - 1] if t > 0 else prmt(edge, U[g][C2 - 1], 0x5432)
-                sel = ((8 | (t >> 2)) | ((8 | (t >> 2)) << 4) |
-                       ((8 | ((t + C2) >> 2)) << 8) | ((8 | ((t + C2) >> 2)) << 12))
-                mk_ = prmt(R[t & 3], R[t & 3], sel)
-                s2 = (mk_ & ma2) | (~mk_ & mi2 & M32)
-                r = max3(iadd32(V[g][t], s2), U[g][t], sh)
+                s2 = substitution(eq7, t, C2, mi2, dm)
+                r = umax3(uadd32(V[g][t], s2), U[g][t], sh)
                 if masked:
                     # slot s lies in the rectangle iff lo <= s <= hi:
                     # max(s - hi - 1, lo - 1 - s) < 0, bounds clamped to 16 bits
@@ -196,18 +255,21 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
                     c = addmax2(mk(-t, -(t + C2)), lo1_2, 0x80008000)
                     u = addmax2(mk(t, t + C2), nhi1_2, c)
                     inside = prmt(u, u, 0xBB99)
-                    r = ((r & inside) | (DEAD2 & ~inside)) & M32
+                    r &= inside
                 idx = (S - 1 - t) | ((S - 1 - (t + C2)) << 16)
-                kc = iadd32(idx, nthr2)
-                key = addmax2(r, kc, 0xFFF0FFF0)
-                pm = prmt(key, key, 0xBB99)
-                newV[g][t] = ((r & ~pm) | (DEAD2 & pm)) & M32
+                key = uadd32(r, uadd32(z, idx))
+                lm = prmt(key, key, 0xBB99)  # 0xFFFF where live
+                newV[g][t] = r & lm
                 keys.append(key)
             kk = keys[0]
             for k_ in keys[1:]:
-                kk = max2(kk, k_)
-            lk = max(halves(kk))
-            lane_keys.append((lk >> 4) * 512 + ((lk & 15) | ((31 - g) << 4)))
+                kk = umax2(kk, k_)
+            lk = max(uhalves(kk))
+            lkey = lk - KEY0
+            lane_bits = ((31 - g) << 4) - (0x800 << 9)
+            mkey = 32 * lk - 31 * (lk & 15) + lane_bits
+            assert mkey == (lkey >> 4) * 512 + ((lkey & 15) | ((31 - g) << 4))
+            lane_keys.append(mkey)
         for g in range(lanes):
             V[g][:] = newV[g]
         mkey = max(lane_keys)
@@ -218,16 +280,16 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
 
     def shift(up):
         if up:  # slot s takes slot s+1
-            ne = [E[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
-            no = [O[g + 1][0] if g + 1 < lanes else DEAD2 for g in range(lanes)]
+            ne = [E[g + 1][0] if g + 1 < lanes else 0 for g in range(lanes)]
+            no = [O[g + 1][0] if g + 1 < lanes else 0 for g in range(lanes)]
             for g in range(lanes):
                 te, to = prmt(E[g][0], ne[g], 0x5432), prmt(O[g][0], no[g], 0x5432)
                 E[g], O[g] = E[g][1:] + [te], O[g][1:] + [to]
                 i0[g] += 1
                 j0[g] -= 1
         else:   # slot s takes slot s-1
-            pe = [E[g - 1][C2 - 1] if g > 0 else DEAD2 for g in range(lanes)]
-            po = [O[g - 1][C2 - 1] if g > 0 else DEAD2 for g in range(lanes)]
+            pe = [E[g - 1][C2 - 1] if g > 0 else 0 for g in range(lanes)]
+            po = [O[g - 1][C2 - 1] if g > 0 else 0 for g in range(lanes)]
             for g in range(lanes):
                 te, to = prmt(pe[g], E[g][C2 - 1], 0x5432), prmt(po[g], O[g][C2 - 1], 0x5432)
                 E[g], O[g] = [te] + E[g][:-1], [to] + O[g][:-1]
@@ -250,12 +312,12 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
             key, ibase, bd = best
             bi = ibase + (31 - ((key >> 4) & 31)) * S + (S - 1 - (key & 15))
             return T, bi, bd - bi, False
-        # Window edges after the even diagonal (live slots hold values >= 0,
-        # pruned ones DEAD < 0).  Up: the top slot of E (diagonal d) or of O
-        # (d-1) is live, and E's two bottom slots and O's bottom slot are
-        # dead.  Down: E's bottom slot is live and the two top slots of E
-        # and of O are dead.  Otherwise, with an edge live, the band has
-        # outgrown the window.
+        # Window edges after the even diagonal (live slots hold values > 0,
+        # pruned ones 0).  Up: the top slot of E (diagonal d) or of O (d-1)
+        # is live, and E's two bottom slots and O's bottom slot are dead.
+        # Down: E's bottom slot is live and the two top slots of E and of O
+        # are dead.  Otherwise, with an edge live, the band has outgrown the
+        # window.
         top, bot = lanes - 1, 0
         need_up = live_hi(E[top][C2 - 1]) or live_hi(O[top][C2 - 1])
         need_dn = live_lo(E[bot][0])
@@ -273,13 +335,13 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
             stats["down"] += 1
             shift(False)
             budget = margin()
-        if thr_o >= kR:  # every live value is >= 16 kR: rebase the frame
+        if thr_o >= kRL:  # every live value is >= 16 (kR + margin): rebase
             stats["rebase"] += 1
-            mr = pack2(-SCALE * kR)
+            mr = pack2(SCALE * kR)
             for g in range(lanes):
                 for t in range(C2):
-                    E[g][t] = addmax2(E[g][t], mr, DEAD2)
-                    O[g][t] = addmax2(O[g][t], mr, DEAD2)
+                    E[g][t] = usub32(umax2(E[g][t], mr), mr)
+                    O[g][t] = usub32(umax2(O[g][t], mr), mr)
             Q -= kR
         if budget < 1:
             budget = margin()

@@ -1,13 +1,15 @@
 """CPU check of the packed 16-bit band arithmetic against the oracle.
 
 ``packed16_model`` restates the kernel's 16-bit arithmetic bit by bit
-(two slots per register, s16x2 ops and carry-free 32-bit adds of packed
-halves, normalised and scaled frame, rebases, packed keys, window shifts
-decided once per pair of diagonals).  On seeded random extensions, including
-scorings at the edges of the packed range, it must reach the oracle's
-(score, best_i, best_j) exactly whenever the band fits the window, and no
-16-bit half may ever wrap.  This pins the exactness argument of the packed
-tiles without a GPU; the GPU tests pin the kernel itself.
+(two slots per register, u16x2 max and carry-free 32-bit adds and
+multiply-adds of packed halves, the biased frame in which a pruned slot
+holds 0, rebases, packed keys, the substitution from multiplied match bits,
+window shifts decided once per pair of diagonals).  On seeded random
+extensions, including scorings at the edges of the packed range, it must
+reach the oracle's (score, best_i, best_j) exactly whenever the band fits
+the window, and no 16-bit half may ever wrap.  This pins the exactness
+argument of the packed tiles without a GPU; the GPU tests pin the kernel
+itself.
 """
 import numpy as np
 import pytest
@@ -48,10 +50,22 @@ def test_scorings_are_in_the_packed_range():
     assert not P.fits(1, -1, -1, 1536) and not P.fits(128, -1, -1, 10)
     assert not P.fits(1, -129, -1, 10) and not P.fits(1, -1, -128, 10)
     assert not P.fits(1, -3, -1, 10)  # mismatch + 2|gap| < 0: 32-bit tiles
-    # the rebase step never falls below 128 inside the range
+    # Over the whole packed range: the rebase step is at least what one pair
+    # of diagonals can add to a threshold (so rebasing keeps up), every
+    # threshold stays <= 2040 (16 thr < 0x8000: pruned keys stay >= 0),
+    # every live value times 16 fits an unsigned half, every key fits 16
+    # bits, and the high-multiply constant of the substitution fits 32 bits.
     for match in range(1, 128):
         for ng in range(1, 129 - match):
-            assert P.rebase_step(match, -ng, 1536 - match) >= 128
+            x = 1536 - match
+            kR = P.rebase_step(match, -ng, x)
+            assert kR >= max(128, match + 2 * ng)
+            thr_max = kR + P.rebase_margin(match) + 2 * match + 3 * ng - 1
+            assert thr_max <= 2040
+            assert P.SCALE * (thr_max + x + match) + P.SCALE * (match + 2 * ng) <= 0xFFFF
+            assert P.KEY0 + P.SCALE * (x + match) + 15 <= 0xFFFF
+            assert P.frame_bias(match, -ng) + ng == match + 2 * ng + 1
+            assert P.SCALE * (match + 128) < 1 << 13  # mismatch >= -128
 
 
 @pytest.mark.parametrize("lanes,regs,seed", [(4, 8, 1), (8, 4, 2)])
