@@ -245,9 +245,10 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
 
 /* Packed tiles: 16-bit cells, two per 32-bit register, for scorings with
  * match - gap <= 128, mismatch >= -128, mismatch - 2*gap >= 0 and
- * x + match <= 1536 (results identical to the 32-bit tiles; other
- * scorings run the 32-bit tile of the same shape).  Set in `cells` of
- * xdrop_set_tile. */
+ * x + match <= 1536, and x + match <= 1022 for the tiles of 32 cells per
+ * lane (results identical to the 32-bit tiles; other scorings run the
+ * packed 16-cell tile of the same width, else the 32-bit tile of that
+ * shape).  Set in `cells` of xdrop_set_tile. */
 #define XDROP_TILE_PACKED16 0x100
 
 /* Batched and plain modes: fix the first band tier to `lanes` lanes per extension
@@ -261,10 +262,12 @@ int xdrop_get_stats(xdrop_ctx *c, xdrop_stats *st);
  * packed tiles when the scoring fits them, else one of every 8 with the
  * 32-bit tiles) and keeps the fastest for that key.  Tiles: 4x16, 8x8, 16x4,
  * 8x16, 16x8, 32x4, and packed (cells | XDROP_TILE_PACKED16) 4x8, 2x16,
- * 4x16, 8x8, 8x16, 16x8.  Returns XDROP_EINVAL for another shape.  Serving mode
- * (set the tile before the first xdrop_submit_pairs) runs packed 4x16 by
- * default; with a packed first tier, requests whose scoring does not fit
- * 16 bits run on the serving kernel's 32-bit second tier. */
+ * 4x16, 8x8, 2x32, 8x16, 16x8, 4x32.  Returns XDROP_EINVAL for another
+ * shape.  Serving mode (set the tile before the first xdrop_submit_pairs)
+ * runs packed 4x16 by default (a packed tile of 32 cells per lane serves as
+ * the 16-cell tile of its width); with a packed first tier, requests whose
+ * scoring does not fit 16 bits run on the serving kernel's 32-bit second
+ * tier. */
 int xdrop_set_tile(xdrop_ctx *c, int lanes, int cells);
 
 /* Several seeds per read pair, keeping the best extension.  Consecutive

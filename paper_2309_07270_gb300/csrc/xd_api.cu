@@ -267,8 +267,8 @@ int enqueue_batched(xdrop_ctx *c, Tile t0, int bps, bool main_events, uint32_t *
 // Candidate first tiles for autotuning (all persistent instantiations);
 // the packed 16-bit ones only for scorings they hold exactly.
 const Tile kTuneTiles[] = {{4, 16}, {8, 8}, {16, 4}, {8, 16}, {16, 8}, {32, 4}};
-const Tile kPackedTiles[] = {{4, 8, true},  {2, 16, true}, {4, 16, true},
-                             {8, 8, true},  {8, 16, true}, {16, 8, true}};
+const Tile kPackedTiles[] = {{4, 8, true},  {2, 16, true}, {4, 16, true}, {8, 8, true},
+                             {2, 32, true}, {8, 16, true}, {16, 8, true}, {4, 32, true}};
 
 // The first tile for a submit: the forced one (unpacked when the scoring
 // does not fit 16 bits) or the tuned one for this scoring.
@@ -315,6 +315,7 @@ int autotune(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *best)
     if (packed) cands.assign(std::begin(kPackedTiles), std::end(kPackedTiles));
     else cands.assign(std::begin(kTuneTiles), std::end(kTuneTiles));
     for (const Tile &t : cands) {
+        if (t.packed && !packed_tile_ok(t, job.sc)) continue;
         const int bps = persistent_blocks_per_sm(t);
         if (bps <= 0) continue;
         float tmin = 1e30f;
@@ -368,8 +369,7 @@ int pick_tile(xdrop_ctx *c, Ticket *tk, const Job &job, Tile *out)
 {
     Tile t = c->forced;
     if (t.lanes) {
-        if (t.packed && !packed_scoring_ok(job.sc)) t.packed = false;
-        *out = t;
+        *out = usable_tile(t, job.sc);
         return XDROP_OK;
     }
     int bucket = 0;
@@ -431,8 +431,7 @@ int run_plain(xdrop_ctx *c, Ticket *tk, const Job &job)
     cudaStream_t s = c->stream;
     const uint64_t n_pairs = job.n_pairs;
     CK(cudaMemsetAsync(c->d_ctrs, 0, C_NBAD * 4, s));
-    Tile t0 = c->forced.lanes ? c->forced : Tile{4, 16, true};
-    if (t0.packed && !packed_scoring_ok(job.sc)) t0.packed = false;
+    const Tile t0 = usable_tile(c->forced.lanes ? c->forced : Tile{4, 16, true}, job.sc);
     c->tile0 = t0;
     const int bps = persistent_blocks_per_sm(t0);
     if (bps <= 0) return fail(XDROP_ECUDA, "tile %dx%d not available", t0.lanes, t0.c);

@@ -40,6 +40,12 @@ int persistent_block_threads(Tile t);  // threads per block of the persistent fi
 int persistent_blocks_per_sm(Tile t);
 // Whether a scoring fits the packed 16-bit tiles exactly.
 bool packed_scoring_ok(const Scoring &sc);
+// A packed tile holds this scoring exactly (lanes of 32 slots need
+// x + match <= 1022 beside packed_scoring_ok).
+bool packed_tile_ok(Tile t, const Scoring &sc);
+// The tile to run for this scoring: t itself if it holds it, else the
+// packed 16-slot tile of the same width, else a 32-bit tile of its width.
+Tile usable_tile(Tile t, const Scoring &sc);
 
 cudaError_t launch_wide(bool count, int grid, const Job *jp, Spill in, int32_t *scratch,
                         int64_t scratch_per_cta, cudaStream_t s);

@@ -162,25 +162,45 @@ __device__ __forceinline__ uint32_t tree_max2(const uint32_t (&k)[N])
 __device__ __forceinline__ bool live_lo(uint32_t v) { return (v & 0xFFFFu) != 0; }
 __device__ __forceinline__ bool live_hi(uint32_t v) { return (v >> 16) != 0; }
 
+// Key units per unit of r, and slot bits of a key: lanes of up to 16 slots
+// keep 16 r and a 4-bit slot index; lanes of 32 slots a 5-bit index, with
+// keys in units of 32 r (the key add doubles the stored value).
+template <int S>
+__host__ __device__ constexpr int key_scale() { return S <= 16 ? 16 : 32; }
+template <int S>
+__host__ __device__ constexpr int slot_bits() { return S <= 16 ? 4 : 5; }
+
 // One anti-diagonal for one lane: V (diagonal d-2, overwritten with d) and
 // U (d-1).  edge: the neighbouring lane's end register of U (next lane's
 // register 0 on odd diagonals, previous lane's register C2-1 on even ones),
-// 0 beyond the group.  eq7: bit 2s+1 set iff slot s's bases match.  k13,
-// k15: 16 (match - mismatch) << 19 and << 17; mi2: the packed mismatch
-// substitution 16 (mismatch + 2|gap|); z: 0x8000 - 16 thr in both halves.
-// Returns the lane's largest key (0 .. 0xFFFF; below 0x8000 iff every slot
-// was pruned).
+// 0 beyond the group.  eq7: bit 2s+1 set iff slot s's bases match (slots
+// 0-15); eqh: the same for slots 16-31 (C2 = 16 only).  k13, k15:
+// 16 (match - mismatch) << 19 and << 17; mi2: the packed mismatch
+// substitution 16 (mismatch + 2|gap|); z: 0x8000 - KS thr in both halves
+// (KS = key_scale).  Returns the lane's largest key (0 .. 0xFFFF; below
+// 0x8000 iff every slot was pruned).
 template <int C2, bool ODD, bool MASKED>
 __device__ __forceinline__ uint32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[C2],
-                                         uint32_t edge, uint32_t eq7, uint32_t mi2,
-                                         uint32_t k13, uint32_t k15, uint32_t z,
+                                         uint32_t edge, uint32_t eq7, uint32_t eqh,
+                                         uint32_t mi2, uint32_t k13, uint32_t k15, uint32_t z,
                                          uint32_t lo1_2, uint32_t nhi1_2, uint32_t one)
 {
-    static_assert(C2 == 4 || C2 == 8, "packed registers per lane");
-    // e: slot t's match bit at 2t+1, slot t+C2's at 2t+17
-    const uint32_t e = (C2 == 4) ? prmt(eq7, eq7, 0x2100) : eq7;
-    const uint32_t es[4] = {fma_add(e, one << 12, 0u), fma_add(e, one << 8, 0u),
-                            fma_add(e, one << 4, 0u), e};
+    static_assert(C2 == 4 || C2 == 8 || C2 == 16, "packed registers per lane");
+    constexpr int NE = C2 == 16 ? 2 : 1;
+    // e[h]: slot t's match bit at 2t+1, slot t+C2's at 2t+17 (registers
+    // 8h .. 8h+7)
+    uint32_t e[NE];
+    if constexpr (C2 == 4) e[0] = prmt(eq7, eq7, 0x2100);
+    else if constexpr (C2 == 8) e[0] = eq7;
+    else { e[0] = prmt(eq7, eqh, 0x5410); e[1] = prmt(eq7, eqh, 0x7632); }
+    uint32_t es[4 * NE];
+#pragma unroll
+    for (int h = 0; h < NE; ++h) {
+        es[4 * h] = fma_add(e[h], one << 12, 0u);
+        es[4 * h + 1] = fma_add(e[h], one << 8, 0u);
+        es[4 * h + 2] = fma_add(e[h], one << 4, 0u);
+        es[4 * h + 3] = e[h];
+    }
     uint32_t key[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) {
@@ -197,8 +217,9 @@ __device__ __forceinline__ uint32_t dp16(uint32_t (&V)[C2], const uint32_t (&U)[
             const uint32_t u = __viaddmax_s16x2(slot2<C2>(t), nhi1_2, c);
             r &= prmt(u, u, 0xBB99);  // 0xFFFF where inside
         }
-        // 0x8000 + 16*(r - thr) + (S-1-slot): bit 15 set iff live
-        const uint32_t k = fma_add(r, one, fma_add(z, one, idx2<C2>(t)));
+        // 0x8000 + KS*(r - thr) + (S-1-slot): bit 15 set iff live
+        const uint32_t k = fma_add(r, (key_scale<2 * C2>() == 16) ? one : one << 1,
+                                   fma_add(z, one, idx2<C2>(t)));
         V[t] = r & prmt(k, k, 0xBB99);
         key[t] = k;
     }
@@ -214,11 +235,22 @@ __host__ __device__ inline bool packed16_ok(const Scoring &sc)
            sc.x >= 0 && sc.x + sc.match <= 1536;
 }
 
+// Lanes of 32 slots keep keys in units of 32 r, so their keys (0x8000 +
+// 32 (x + match) + 31 at most) need x + match <= 1022 as well.
+__host__ __device__ inline bool packed32_ok(const Scoring &sc)
+{
+    return packed16_ok(sc) && sc.x + sc.match <= 1022;
+}
+
 // Frame step of one rebase (units of r) for a scoring that passes
-// packed16_ok: between 1656 and 2033 there (see the header comment's ranges).
+// packed16_ok: the threshold cap 0x8000 / KS - 8 (2040 or 1016) less
+// 3 match + 3|gap|, so between 1656 and 2033 for lanes of up to 16 slots
+// and between 632 and 1009 for lanes of 32 (see the header comment's
+// ranges).
+template <int S>
 __host__ __device__ inline int32_t rebase_step16(const Scoring &sc)
 {
-    return 2040 - 3 * sc.match + 3 * sc.gap;
+    return (0x8000 / p16::key_scale<S>() - 8) - 3 * sc.match + 3 * sc.gap;
 }
 
 // one: 1 (see fma_add).
@@ -229,7 +261,13 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     using namespace p16;
     constexpr int S = 2 * C2;  // slots per lane
     constexpr int W = L * S;
-    static_assert(S <= 16 && 32 % L == 0 && L >= 2 && C2 % 4 == 0, "packed tile shape");
+    constexpr bool WIDE = S == 32;              // two base-window words per read
+    constexpr int SB = slot_bits<S>();          // slot bits of a key
+    constexpr int VS = SB + 5;                  // value shift of a group key
+    constexpr uint32_t SMASK = (1u << SB) - 1u;
+    // -KS * 0x10001: z = 0x80008000 - KS thr in both halves
+    constexpr uint32_t ZMUL = 0u - (uint32_t)key_scale<S>() * 0x10001u;
+    static_assert(S <= 32 && 32 % L == 0 && L >= 2 && C2 % 4 == 0, "packed tile shape");
     const int lane = threadIdx.x & 31;
     const int glane = lane % L;
     const int gbase = lane - glane;
@@ -250,7 +288,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     int32_t mn = 0, m = 0, n = 0, d = 0, i0 = 0, j0 = 0, T = 0, bi = 0, bj = 0;
     int32_t Q = 0;                      // frame offset: thr = T + Q
     int32_t kR = 0, kRL = 0;            // rebase step, and the threshold that triggers one
-    int32_t xup = 0;                    // (x + 1) * 512: a group key this large raises T
+    int32_t xup = 0;                    // (x + 1) << VS: a group key this large raises T
     int32_t bkey = 0, bi0 = 0, bd = 0;  // best cell: group key, this lane's i0, diagonal
     int32_t ng = 1;                     // |gap|
     uint32_t mi2 = 0;                   // packed 16 * (mismatch + 2|gap|)
@@ -259,15 +297,17 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
     uint32_t E[C2], O[C2];
 #pragma unroll
     for (int t = 0; t < C2; ++t) { E[t] = 0u; O[t] = 0u; }
-    uint32_t Aw = 0, LA = 0, Bw = 0, LB = 0;
+    // base windows (slots 0-15; Aw1, Bw1: slots 16-31 of 32-slot lanes) and
+    // the lookahead words
+    uint32_t Aw = 0, Aw1 = 0, LA = 0, Bw = 0, Bw1 = 0, LB = 0;
     int la_n = 16;        // warp-uniform: diagonal pairs the lookahead words still cover
     int32_t budget = 0;   // warp-uniform: diagonal pairs known to stay inside every rectangle
     // (31 - lane) * 16, less the key offset's share of the group key
-    const int32_t lane_bits = ((31 - glane) << 4) - (0x800 << 9);
+    const int32_t lane_bits = ((31 - glane) << SB) - (0x8000 << 5);
 
     auto retire = [&](bool overflow) {
         if (bd > 0) {
-            bi = (bi0 - glane * S) + (31 - ((bkey >> 4) & 31)) * S + (S - 1 - (bkey & 15));
+            bi = (bi0 - glane * S) + (31 - ((bkey >> SB) & 31)) * S + (S - 1 - (int)(bkey & SMASK));
             bj = bd - bi;
         }
         if (glane == 0) src.retire(gj, task, overflow, T, bi, bj);
@@ -283,6 +323,19 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         budget = __reduce_min_sync(FULL, active ? mg : INT32_MAX);
     };
 
+    // The base windows of this lane's slots at the current i0, j0: slot s
+    // holds a[i0 + s] and b[j0 - s]; the lookahead words the next 16 bases.
+    auto load_windows = [&]() {
+        Aw = fwd16_u(pk, nw, sa0, dir, i0);
+        Bw = back16_u(pk, nw, sb0, dir, j0);
+        if constexpr (WIDE) {
+            Aw1 = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+            Bw1 = back16_u(pk, nw, sb0, dir, j0 - 16);
+        }
+        LA = fwd16_u(pk, nw, sa0, dir, i0 + (WIDE ? 32 : 16));
+        LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+    };
+
     // One anti-diagonal and the bookkeeping that cannot wait for the end of
     // the pair: T and the best cell.  Returns the group key (negative iff
     // every cell of the diagonal was pruned) and the diagonal's threshold.
@@ -293,16 +346,22 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         Q += ng;
         if (ODD) {
             ++i0;
-            Aw = __funnelshift_r(Aw, LA, 2);
+            if constexpr (WIDE) {
+                Aw = __funnelshift_r(Aw, Aw1, 2);
+                Aw1 = __funnelshift_r(Aw1, LA, 2);
+            } else {
+                Aw = __funnelshift_r(Aw, LA, 2);
+            }
             LA >>= 2;
         } else {
             ++j0;
+            if constexpr (WIDE) Bw1 = __funnelshift_l(Bw, Bw1, 2);
             Bw = __funnelshift_l(LB, Bw, 2);
             LB <<= 2;
         }
         thr = T + Q;
         // 0x8000 - 16 thr in both halves (no borrow: 16 thr <= 0x8000)
-        const uint32_t z = (uint32_t)thr * 0xFFEFFFF0u + kKey2;
+        const uint32_t z = (uint32_t)thr * ZMUL + kKey2;
         // rectangle bounds of this lane's slots, clamped into 16 bits (only
         // the masked copy reads them)
         uint32_t lo1_2 = 0, nhi1_2 = 0;
@@ -313,21 +372,29 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
         }
         const uint32_t xx = Aw ^ Bw;
         const uint32_t eq7 = ~(xx | (xx << 1));
+        uint32_t eqh = 0u;
+        if constexpr (WIDE) {
+            const uint32_t xh = Aw1 ^ Bw1;
+            eqh = ~(xh | (xh << 1));
+        }
         uint32_t lk;
         if (ODD) {
             const uint32_t edge = fma_add(__shfl_down_sync(FULL, E[0], 1, L), keep_up, 0u);
-            lk = dp16<C2, true, MASKED>(O, E, edge, eq7, mi2, k13, k15, z, lo1_2, nhi1_2, one);
+            lk = dp16<C2, true, MASKED>(O, E, edge, eq7, eqh, mi2, k13, k15, z, lo1_2, nhi1_2,
+                                        one);
         } else {
             const uint32_t edge = fma_add(__shfl_up_sync(FULL, O[C2 - 1], 1, L), keep_dn, 0u);
-            lk = dp16<C2, false, MASKED>(E, O, edge, eq7, mi2, k13, k15, z, lo1_2, nhi1_2, one);
+            lk = dp16<C2, false, MASKED>(E, O, edge, eq7, eqh, mi2, k13, k15, z, lo1_2, nhi1_2,
+                                         one);
         }
         // Group key: value above lane above slot in lane, so one max finds
         // the lowest window slot among the cells holding the maximum.  With
-        // lk = 16 v + i: 32 lk - 31 i = 512 v + i (multiply-adds).
+        // lk = 0x8000 + 2^SB v + i: 32 lk - 31 i = 0x8000 * 32 + 2^VS v + i
+        // (multiply-adds).
         const int32_t mkey = lockstep_group_max<L>(
-            (int32_t)fma_add(lk, one << 5, fma_add(lk & 15u, 0u - 31u, (uint32_t)lane_bits)));
+            (int32_t)fma_add(lk, one << 5, fma_add(lk & SMASK, 0u - 31u, (uint32_t)lane_bits)));
         if (mkey >= xup) {  // best value - thr > x: T rises (decoded at retire)
-            T += (mkey >> 9) - sc.x;
+            T += (mkey >> VS) - sc.x;
             bkey = mkey;
             bi0 = i0;
             bd = d;
@@ -414,17 +481,14 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                 }
             }
             if (su || sd) {
-                Aw = fwd16_u(pk, nw, sa0, dir, i0);
-                LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
-                Bw = back16_u(pk, nw, sb0, dir, j0);
-                LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+                load_windows();
             }
             fin = fin || ovf;
         }
         if (fin) retire(ovf);
         const bool refill = la_n == 0;
         if (refill) {
-            LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
+            LA = fwd16_u(pk, nw, sa0, dir, i0 + (WIDE ? 32 : 16));
             LB = back16_u(pk, nw, sb0, dir, j0 + 16);
             la_n = 16;
         }
@@ -474,7 +538,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                     exhausted = true;
                 } else if (r > 0) {
                     const Ext e = src.open(gj, task, sc);
-                    if (e.ok && !packed16_ok(sc)) {
+                    if (e.ok && !(WIDE ? packed32_ok(sc) : packed16_ok(sc))) {
                         // A scoring 16-bit cells cannot hold exactly (a serving
                         // request's own): hand the task to the next, 32-bit tier.
                         if (glane == 0) src.retire(gj, task, true, 0, 0, 0);
@@ -486,9 +550,9 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         n = e.n;
                         mn = m + n;
                         ng = -sc.gap;
-                        kR = rebase_step16(sc);
+                        kR = rebase_step16<S>(sc);
                         kRL = kR + sc.match + 1;
-                        xup = (sc.x + 1) * 512;
+                        xup = (sc.x + 1) << VS;
                         mi2 = pack2(kScale * (sc.mismatch + 2 * ng));
                         k13 = (uint32_t)(kScale * (sc.match - sc.mismatch)) << 19;
                         k15 = (uint32_t)(kScale * (sc.match - sc.mismatch)) << 17;
@@ -506,10 +570,7 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
                         }
                         i0 = -(W / 2) + glane * S;
                         j0 = (W / 2) - glane * S;
-                        Aw = fwd16_u(pk, nw, sa0, dir, i0);
-                        LA = fwd16_u(pk, nw, sa0, dir, i0 + 16);
-                        Bw = back16_u(pk, nw, sb0, dir, j0);
-                        LB = back16_u(pk, nw, sb0, dir, j0 + 16);
+                        load_windows();
                         d = 0;
                         T = 0;
                         Q = beta;
@@ -541,9 +602,9 @@ __device__ __forceinline__ void lockstep16_loop(Src &src, const uint32_t *pk, in
 }
 
 // Batched form of the packed kernel (same task source as lockstep_kernel).
-// 128-thread blocks: with the FMA-pipe adds the loop holds about 85
-// registers, five such blocks fit an SM (20 warps), and that measured faster
-// than capping the registers for more warps.
+// 128-thread blocks: the loop holds about 96 registers with 16 slots per
+// lane (five such blocks fit an SM, 20 warps) and 128 with 32 (four blocks),
+// and that measured faster than capping the registers for more warps.
 constexpr int kPackedThreads = 128;
 template <int L, int C2>
 __global__ void __launch_bounds__(kPackedThreads)

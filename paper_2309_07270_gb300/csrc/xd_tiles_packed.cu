@@ -1,6 +1,7 @@
 // Packed 16-bit band tiles (two window slots per register): 4x8 and 2x16
-// (width 32, narrow bands such as x = 15), 4x16 and 8x8 (width 64), 8x16
-// and 16x8 (width 128).
+// (width 32, narrow bands such as x = 15), 4x16, 8x8 and 2x32 (width 64),
+// 8x16, 16x8 and 4x32 (width 128).  Lanes of 32 slots spread each
+// diagonal's per-lane bookkeeping over twice the cells.
 #include "xd_launch.h"
 #include "xd_serve_kernels.cuh"
 
@@ -35,6 +36,8 @@ cudaError_t launch_persistent_packed(Tile t, int grid, const Job *jp, const uint
         if (t.lanes == 8 && t.c == 8) return packed_impl<8, 4>(grid, jp, order, n, ctr, sp, s);
         if (t.lanes == 8 && t.c == 16) return packed_impl<8, 8>(grid, jp, order, n, ctr, sp, s);
         if (t.lanes == 16 && t.c == 8) return packed_impl<16, 4>(grid, jp, order, n, ctr, sp, s);
+        if (t.lanes == 2 && t.c == 32) return packed_impl<2, 16>(grid, jp, order, n, ctr, sp, s);
+        if (t.lanes == 4 && t.c == 32) return packed_impl<4, 16>(grid, jp, order, n, ctr, sp, s);
     }
     *handled = false;
     return cudaSuccess;
@@ -49,10 +52,28 @@ int occupancy_packed(Tile t)
     if (t.lanes == 8 && t.c == 8) return packed_occupancy_impl<8, 4>();
     if (t.lanes == 8 && t.c == 16) return packed_occupancy_impl<8, 8>();
     if (t.lanes == 16 && t.c == 8) return packed_occupancy_impl<16, 4>();
+    if (t.lanes == 2 && t.c == 32) return packed_occupancy_impl<2, 16>();
+    if (t.lanes == 4 && t.c == 32) return packed_occupancy_impl<4, 16>();
     return -1;
 }
 
 bool packed_scoring_ok(const Scoring &sc) { return packed16_ok(sc); }
+
+bool packed_tile_ok(Tile t, const Scoring &sc)
+{
+    return t.packed && (t.c == 32 ? packed32_ok(sc) : packed16_ok(sc));
+}
+
+Tile usable_tile(Tile t, const Scoring &sc)
+{
+    if (!t.packed || packed_tile_ok(t, sc)) return t;
+    if (t.c == 32) {  // the 16-slot tile of the same width, or its 32-bit twin
+        const Tile h{2 * t.lanes, 16, true};
+        return packed16_ok(sc) ? h : Tile{h.lanes, 16, false};
+    }
+    if (t.width() < 64) return Tile{4, 16, false};  // no 32-bit tile this narrow
+    return Tile{t.lanes, t.c, false};
+}
 
 int persistent_block_threads(Tile t) { return t.packed ? kPackedThreads : 256; }
 
@@ -80,6 +101,8 @@ cudaError_t launch_serve_packed(Tile t, int grid, const ServeArgs &a, const uint
 {
     *handled = true;
     if (t.packed) {
+        // lanes of 32 slots serve as the 16-slot tile of the same width
+        if (t.c == 32) t = Tile{2 * t.lanes, 16, true};
         if (t.lanes == 4 && t.c == 16) return serve16_impl<4, 8, 16, 8>(grid, a, pk, nw, s);
         if (t.lanes == 8 && t.c == 8) return serve16_impl<8, 4, 16, 8>(grid, a, pk, nw, s);
         if (t.lanes == 8 && t.c == 16) return serve16_impl<8, 8, 32, 16>(grid, a, pk, nw, s);
@@ -92,6 +115,7 @@ cudaError_t launch_serve_packed(Tile t, int grid, const ServeArgs &a, const uint
 int serve_occupancy_packed(Tile t)
 {
     if (!t.packed) return -1;
+    if (t.c == 32) t = Tile{2 * t.lanes, 16, true};
     if (t.lanes == 4 && t.c == 16) return serve16_occupancy_impl<4, 8, 16, 8>();
     if (t.lanes == 8 && t.c == 8) return serve16_occupancy_impl<8, 4, 16, 8>();
     if (t.lanes == 8 && t.c == 16) return serve16_occupancy_impl<8, 8, 32, 16>();

@@ -110,16 +110,28 @@ def pack2(v):
     return ((v & 0xFFFF) * 0x10001) & M32
 
 
-def fits(match, mismatch, gap, x):
-    """The packed tiles' range (packed16_ok in the kernel)."""
-    return (match - gap <= 128 and mismatch >= -128 and mismatch - 2 * gap >= 0 and x >= 0
-            and x + match <= 1536)
+def fits(match, mismatch, gap, x, slots=16):
+    """The packed tiles' range (packed16_ok in the kernel); tiles with 32
+    slots per lane also need x + match <= 1022 (their keys carry 5 slot
+    bits)."""
+    ok = (match - gap <= 128 and mismatch >= -128 and mismatch - 2 * gap >= 0 and x >= 0
+          and x + match <= 1536)
+    return ok and (slots <= 16 or x + match <= 1022)
 
 
-def rebase_step(match, gap, x):
+def key_scale(slots):
+    """Key units per unit of r: 16 for up to 16 slots per lane, 32 for 32."""
+    return 16 if slots <= 16 else 32
+
+
+def slot_bits(slots):
+    return 4 if slots <= 16 else 5
+
+
+def rebase_step(match, gap, x, slots=16):
     """The frame step of one rebase (rebase_step16 in the kernel)."""
     ng = -gap
-    return 2040 - 3 * match - 3 * ng
+    return (0x8000 // key_scale(slots) - 8) - 3 * match - 3 * ng
 
 
 def frame_bias(match, gap):
@@ -143,14 +155,19 @@ def live_hi(v):
 
 
 # Substitution of register t from the match bits.  e holds slot t's match
-# bit at 2t+1 and slot t+C2's at 2t+17 (for C2 = 4 after one byte permute).
+# bit at 2t+1 and slot t+C2's at 2t+17 (for C2 = 4 after one byte permute;
+# for C2 = 16 registers 0-7 and 8-15 each take one of two byte-permuted
+# merges of the two match words, eq7 of slots 0-15 and eqh of slots 16-31).
 # Shifted left by 12 - 4*(t >> 1), the two bits sit at p = 13 + 2*(t & 1)
 # and p + 16; a high multiply by dm * 2^(32-p), with dm = 16 (match -
 # mismatch) < 2^13, turns them into the per-half match bonus, and the
 # multiply-add's addend is the mismatch substitution.
-def substitution(eq7, t, C2, mi2, dm):
+def substitution(eq7, t, C2, mi2, dm, eqh=0):
     if C2 == 4:
         e = prmt(eq7, eq7, 0x2100)  # bytes 0, 0, 1, 2: slot t+4 moves up by 8
+    elif C2 == 16:
+        e = prmt(eq7, eqh, 0x5410) if t < 8 else prmt(eq7, eqh, 0x7632)
+        t &= 7
     else:
         e = eq7
     sh, p = 12 - 4 * (t >> 1), 13 + 2 * (t & 1)
@@ -173,13 +190,14 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
         stats = {}
     for k in ("up", "down", "rebase", "masked"):
         stats.setdefault(k, 0)
-    assert fits(match, mismatch, gap, x)
     C2, S = regs, 2 * regs
-    assert C2 in (4, 8)
+    assert C2 in (4, 8, 16)
+    assert fits(match, mismatch, gap, x, S)
+    KS, SB = key_scale(S), slot_bits(S)
     W = lanes * S
     m, n = len(a), len(b)
     ng = -gap
-    kR = rebase_step(match, gap, x)
+    kR = rebase_step(match, gap, x, S)
     kRL = kR + rebase_margin(match)
     assert kR >= match + 2 * ng
 
@@ -224,16 +242,19 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
             raise AssertionError("unmasked diagonal leaves the rectangle")
         V, U = (O, E) if odd else (E, O)
         thr = T + Q
-        if not match + 2 * ng + 1 <= thr <= 2048:
+        if not match + 2 * ng + 1 <= thr <= 0x8000 // KS:
             raise Wrap(("threshold", thr))
-        z = umk(KEY0 - SCALE * thr, KEY0 - SCALE * thr)  # 0x80008000 - 16 thr * 0x10001
+        z = umk(KEY0 - KS * thr, KEY0 - KS * thr)  # 0x80008000 - KS thr * 0x10001
         lane_keys = []
         newV = [list(v) for v in V]
         for g in range(lanes):
-            xx = 0  # the kernel's base windows hold 2-bit fields
-            for s in range(16):
-                xx |= ((base_a(i0[g] + s) ^ base_b(j0[g] - s)) & 3) << (2 * s)
-            eq7 = ~(xx | (xx << 1)) & M32  # bit 2s+1: slot s matches
+            eqs = []  # the kernel's base windows hold 2-bit fields, 16 slots a word
+            for w0 in range(0, max(S, 16), 16):
+                xx = 0
+                for s in range(16):
+                    xx |= ((base_a(i0[g] + w0 + s) ^ base_b(j0[g] - w0 - s)) & 3) << (2 * s)
+                eqs.append(~(xx | (xx << 1)) & M32)  # bit 2s+1: slot w0+s matches
+            eq7, eqh = eqs[0], eqs[-1]
             if odd:
                 edge = U[g + 1][0] if g + 1 < lanes else 0
             else:
@@ -244,7 +265,7 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
                     sh = U[g][t + 1] if t + 1 < C2 else prmt(U[g][0], edge, 0x5432)
                 else:
                     sh = U[g][t - 1] if t > 0 else prmt(edge, U[g][C2 - 1], 0x5432)
-                s2 = substitution(eq7, t, C2, mi2, dm)
+                s2 = substitution(eq7, t, C2, mi2, dm, eqh)
                 r = umax3(uadd32(V[g][t], s2), U[g][t], sh)
                 if masked:
                     # slot s lies in the rectangle iff lo <= s <= hi:
@@ -257,7 +278,7 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
                     inside = prmt(u, u, 0xBB99)
                     r &= inside
                 idx = (S - 1 - t) | ((S - 1 - (t + C2)) << 16)
-                key = uadd32(r, uadd32(z, idx))
+                key = uadd32(r if KS == 16 else uadd32(r, r), uadd32(z, idx))
                 lm = prmt(key, key, 0xBB99)  # 0xFFFF where live
                 newV[g][t] = r & lm
                 keys.append(key)
@@ -266,15 +287,16 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
                 kk = umax2(kk, k_)
             lk = max(uhalves(kk))
             lkey = lk - KEY0
-            lane_bits = ((31 - g) << 4) - (0x800 << 9)
-            mkey = 32 * lk - 31 * (lk & 15) + lane_bits
-            assert mkey == (lkey >> 4) * 512 + ((lkey & 15) | ((31 - g) << 4))
+            smask = (1 << SB) - 1
+            lane_bits = ((31 - g) << SB) - 32 * KEY0
+            mkey = 32 * lk - 31 * (lk & smask) + lane_bits
+            assert mkey == (lkey >> SB) * (1 << (SB + 5)) + ((lkey & smask) | ((31 - g) << SB))
             lane_keys.append(mkey)
         for g in range(lanes):
             V[g][:] = newV[g]
         mkey = max(lane_keys)
-        if mkey >= (x + 1) * 512:  # the diagonal's best value exceeds T
-            T = T - x + (mkey >> 9)
+        if mkey >= (x + 1) << (SB + 5):  # the diagonal's best value exceeds T
+            T = T - x + (mkey >> (SB + 5))
             best = (mkey, i0[0], d)
         return mkey, thr
 
@@ -310,7 +332,7 @@ def extend(a, b, match, mismatch, gap, x, lanes=4, regs=8, stats=None):
             if best is None:
                 return T, 0, 0, False
             key, ibase, bd = best
-            bi = ibase + (31 - ((key >> 4) & 31)) * S + (S - 1 - (key & 15))
+            bi = ibase + (31 - ((key >> SB) & 31)) * S + (S - 1 - (key & ((1 << SB) - 1)))
             return T, bi, bd - bi, False
         # Window edges after the even diagonal (live slots hold values > 0,
         # pruned ones 0).  Up: the top slot of E (diagonal d) or of O (d-1)

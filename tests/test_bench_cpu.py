@@ -54,9 +54,10 @@ def test_committed_traffic_file_parses():
 
 def test_committed_traffic_matches_the_current_kernel_sources():
     """The DRAM traffic in profiles/traffic.txt was measured on the kernel
-    sources as they are: the default bench line can use it."""
+    sources as they are, for the first-tier kernel the default bench line
+    runs (packed 2 lanes x 32 cells at X = 50): the line can use it."""
     bench = load_bench()
-    assert bench.traffic_from_profile("lockstep16_kernel<4,8>") is not None
+    assert bench.traffic_from_profile("lockstep16_kernel<2,16>") is not None
 
 
 def test_seed_discovery_failure_is_reported_not_raised(monkeypatch):

@@ -71,7 +71,7 @@ def test_genome_29x_every_pair(X, oracle_full, genome29, x):
 
 
 TILES = [(4, 16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16), (4, 8 | P16),
-         (2, 16 | P16)]
+         (2, 16 | P16), (2, 32 | P16), (4, 32 | P16)]
 
 
 @pytest.mark.parametrize("x", [50, 100])

@@ -110,7 +110,8 @@ def test_other_scorings(X, aligners, orc, mode, scores):
 
 P16 = 0x100  # XDROP_TILE_PACKED16
 TILES = [(4, 16), (8, 8), (16, 4), (8, 16), (16, 8), (32, 4),
-         (4, 8 | P16), (2, 16 | P16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16)]
+         (4, 8 | P16), (2, 16 | P16), (4, 16 | P16), (8, 8 | P16), (8, 16 | P16), (16, 8 | P16),
+         (2, 32 | P16), (4, 32 | P16)]
 
 
 def tile_id(t):
@@ -155,6 +156,48 @@ def test_packed_tiles_at_their_limits(X, orc, tile, scores):
             got = run_host(X, al, w)
             assert al.tile() == tile
             assert_same(got, oracle_results(orc, w), f"{tile_id(tile)} {scores} {w.name}")
+
+
+# The same limits for the tiles of 32 cells per lane, whose keys also need
+# x + match <= 1022.
+PACKED32_LIMIT_SCORINGS = [
+    (64, -128, -64, 958),   # every limit at once
+    (1, -2, -1, 1021),      # largest x
+    (3, -2, -125, 100),
+    (127, -1, -1, 895),     # largest match
+    (1, 0, -1, 50),
+    (7, -1, -2, 0),
+]
+
+
+@pytest.mark.parametrize("scores", PACKED32_LIMIT_SCORINGS, ids=lambda s: "_".join(map(str, s)))
+@pytest.mark.parametrize("tile", [(2, 32 | P16), (4, 32 | P16)], ids=tile_id)
+def test_packed32_tiles_at_their_limits(X, orc, tile, scores):
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        al.set_tile(*tile)
+        for w in (W.template_pairs(n_pairs=24, len_lo=1500, len_hi=3000, seed=34),
+                  W.tiny_pairs(n_pairs=150, seed=35, x=9)):
+            w.match, w.mismatch, w.gap, w.x = scores
+            got = run_host(X, al, w)
+            assert al.tile() == tile
+            assert_same(got, oracle_results(orc, w), f"{tile_id(tile)} {scores} {w.name}")
+
+
+@pytest.mark.parametrize("scores,want_tile", [((1, -1, -1, 1022), (4, 16 | P16)),
+                                              ((127, -1, -1, 896), (4, 16 | P16)),
+                                              ((1, -3, -1, 30), (4, 16))],
+                         ids=["x1022", "match127_x896", "not16bit"])
+def test_packed32_tile_falls_back_outside_its_range(X, orc, scores, want_tile):
+    """A forced 2x32 packed tile runs the packed 4x16 tile (same width) when
+    x + match exceeds 1022, and the 32-bit 4x16 tile when the scoring does
+    not fit 16 bits at all; the results are the same."""
+    with X.Aligner(mode=X.XDROP_MODE_BATCHED) as al:
+        al.set_tile(2, 32 | P16)
+        w = W.template_pairs(n_pairs=12, len_lo=300, len_hi=800, seed=36)
+        w.match, w.mismatch, w.gap, w.x = scores
+        got = run_host(X, al, w)
+        assert al.tile() == want_tile
+        assert_same(got, oracle_results(orc, w), f"fallback {scores}")
 
 
 @pytest.mark.parametrize("scores", [(1, -1, -1, 1536), (128, -1, -1, 10), (1, -129, -1, 10),

@@ -29,10 +29,11 @@ SCORINGS = [
 ]
 
 
-def cases(seed, n):
+def cases(seed, n, slots=16):
     rng = np.random.default_rng(seed)
+    scorings = [sc for sc in SCORINGS if P.fits(*sc, slots)]
     for k in range(n):
-        sc = SCORINGS[k % len(SCORINGS)]
+        sc = scorings[k % len(scorings)]
         la, lb = int(rng.integers(0, 260)), int(rng.integers(0, 260))
         t = rng.integers(0, 4, max(la, lb) + 40).astype(np.uint8)
         kind = k % 3
@@ -66,12 +67,24 @@ def test_scorings_are_in_the_packed_range():
             assert P.KEY0 + P.SCALE * (x + match) + 15 <= 0xFFFF
             assert P.frame_bias(match, -ng) + ng == match + 2 * ng + 1
             assert P.SCALE * (match + 128) < 1 << 13  # mismatch >= -128
+    # Lanes of 32 slots: keys in units of 32 r, thresholds <= 1016, and
+    # x + match <= 1022 keeps every key within 16 bits.
+    for match in range(1, 128):
+        for ng in range(1, 129 - match):
+            x = 1022 - match
+            assert P.fits(match, -1, -ng, x, 32) and not P.fits(match, -1, -ng, x + 1, 32)
+            kR = P.rebase_step(match, -ng, x, 32)
+            assert kR >= max(128, match + 2 * ng)
+            thr_max = kR + P.rebase_margin(match) + 2 * match + 3 * ng - 1
+            assert P.key_scale(32) * thr_max <= P.KEY0
+            assert P.KEY0 + P.key_scale(32) * (x + match) + 31 <= 0xFFFF
+            assert 2 * P.SCALE * (thr_max + x + match) <= 0xFFFF
 
 
-@pytest.mark.parametrize("lanes,regs,seed", [(4, 8, 1), (8, 4, 2)])
+@pytest.mark.parametrize("lanes,regs,seed", [(4, 8, 1), (8, 4, 2), (2, 16, 3)])
 def test_model_matches_oracle(orc, lanes, regs, seed):
     done = overflow = 0
-    for sc, a, b in cases(seed, 48):
+    for sc, a, b in cases(seed, 48, 2 * regs):
         want = orc.extend(a, b, *sc)[:3]
         got = P.extend(a, b, *sc, lanes=lanes, regs=regs)
         if got[3]:
@@ -102,7 +115,7 @@ def _drifting(t, rng, every):
     return np.concatenate(out)
 
 
-@pytest.mark.parametrize("lanes,regs", [(4, 8), (2, 8)])
+@pytest.mark.parametrize("lanes,regs", [(4, 8), (2, 8), (2, 16)])
 def test_model_drifting_band_shifts_the_window(orc, lanes, regs):
     """One read gains a base every 8 (then the other does): the optimal
     path drifts one diagonal per 8 bases, so the window must shift many
