@@ -4,7 +4,8 @@
 // results as lockstep_loop (xd_device.cuh); only the arithmetic changes.
 // It is exact whenever the scoring passes packed16_ok():
 //   match - gap <= 128, mismatch >= -128, mismatch + 2|gap| >= 0,
-//   x + match <= 1536.
+//   x + match <= 1536,
+// and, for lanes of 32 slots, packed32_ok(): also x + match <= 1022.
 //
 // Biased, normalised scores.  A live cell on anti-diagonal d holds
 //   r = H + x + d*|gap| - B + beta     (B: the rebase steps taken off,
@@ -21,20 +22,25 @@
 // live predecessor stays pruned, and one with a live predecessor takes the
 // same maximum as the recurrence over live predecessors.
 //
-// Key.  One more 32-bit add gives each slot's key
-//   0x8000 + 16*(r - thr) + (S-1-slot),
-// which has bit 15 set exactly for the live cells (a byte permute spreads
-// that bit into the mask that zeroes the pruned ones) and, for live cells,
+// Key.  One more 32-bit multiply-add gives each slot's key
+//   0x8000 + KS*(r - thr) + (S-1-slot),
+// with KS = 16 key units per unit of r for lanes of up to 16 slots (a
+// 4-bit slot index; the add takes the stored 16 r as it is) and KS = 32
+// for lanes of 32 (a 5-bit index; the multiply-add doubles 16 r).  Bit 15
+// is set exactly for the live cells (a byte permute spreads that bit into
+// the mask that zeroes the pruned ones) and, for live cells, the key
 // orders by value and then by lowest slot.  The lane's best key becomes
-// value * 512 + (31 - lane) * 16 + (key & 15) in 32 bits, value = key/16 -
-// 0x800, so one group max gives the largest value and, among equal values,
-// the lowest window slot: the first cell in order of increasing i on the
-// diagonal.
+// value * 2^(SB+5) + (31 - lane) * 2^SB + slot bits in 32 bits (SB = 4 or
+// 5 slot bits), so one group max gives the largest value and, among equal
+// values, the lowest window slot: the first cell in order of increasing i
+// on the diagonal.
 //
-// Substitution.  The match bits of the lane's 16 slots come from one XOR of
-// the 2-bit base windows.  For register t the two bits (slots t and t+C2)
-// are moved to bits p and p+16, p = 13 or 15, by a left shift (a multiply
-// on the FMA pipe) and masked; a high multiply by 16 (match - mismatch) *
+// Substitution.  The match bits of each 16 slots of a lane come from one
+// XOR of two 2-bit base-window words (a lane of 32 slots keeps two words
+// per read, and byte permutes merge its two match words for each half of
+// its 16 registers).  For register t the two bits (slots t and t+C2) are
+// moved to bits p and p+16, p = 13 or 15, by a left shift (a multiply on
+// the FMA pipe) and masked; a high multiply by 16 (match - mismatch) *
 // 2^(32-p) turns them into the per-half match bonus, and its addend is the
 // mismatch substitution.  One ALU instruction (the mask) per register.
 //
@@ -44,9 +50,12 @@
 // register t sits in register t+1 (t-1) at the same half; only the end
 // registers need a byte permute and one shuffle per diagonal.
 //
-// Ranges, in units of r, with kR = 2040 - 3 match - 3|gap| the rebase step
-// (rebase_step16: at least 1656 inside the range above, and at least
-// match + 2|gap|, the most one pair of diagonals can raise a threshold).
+// Ranges, in units of r, with kR = (0x8000 / KS - 8) - 3 match - 3|gap|
+// the rebase step (rebase_step16: at least 1656 for KS = 16 and 632 for
+// KS = 32 inside the ranges above, and at least match + 2|gap|, the most
+// one pair of diagonals can raise a threshold); the figures below are for
+// KS = 16, and for KS = 32 they halve (thresholds <= 1016, keys below
+// 2^16 by x + match <= 1022, 32 r below 2^16).
 // After every pair of diagonals (odd d-1, even d) the frame is rebased by
 // kR once thr of d-1 reaches kR + match + 1.  Every live value of d-1 and d
 // is at least that threshold, so it stays above match + 1 > 0 after the
