@@ -95,15 +95,23 @@ def test_model_matches_oracle(orc, lanes, regs, seed):
     assert done >= 30 and overflow <= 18
 
 
-def test_model_long_identical_reads_rebase_many_times(orc):
+@pytest.mark.parametrize("lanes,regs,scorings", [
+    (4, 8, [(127, -1, -1, 1409), (64, -128, -64, 1472)]),
+    (2, 16, [(127, -1, -1, 895), (64, -128, -64, 958)]),  # x + match <= 1022
+])
+def test_model_long_identical_reads_rebase_many_times(orc, lanes, regs, scorings):
     """Identical 1,500-base reads with the largest match: the score
-    grows by 127 per diagonal pair, so the frame is rebased over and over."""
+    grows by up to 127 per diagonal pair, so the frame is rebased over and
+    over: every 9 to 13 pairs with 16-slot lanes, every 3 to 5 with 32-slot
+    ones, whose keys leave half the threshold range."""
     rng = np.random.default_rng(9)
     t = rng.integers(0, 4, 1500).astype(np.uint8)
-    for sc in [(127, -1, -1, 1409), (64, -128, -64, 1472)]:
+    for sc in scorings:
         want = orc.extend(t, t, *sc)[:3]
-        got = P.extend(t, t, *sc, lanes=4, regs=8)
+        st = {}
+        got = P.extend(t, t, *sc, lanes=lanes, regs=regs, stats=st)
         assert not got[3] and tuple(got[:3]) == tuple(want), (sc, got, want)
+        assert st["rebase"] >= 100, st
 
 
 def _drifting(t, rng, every):
